@@ -1,0 +1,323 @@
+"""Benchmark: voxel-transducer pairs/s of the closed-form operator A and its
+adjoint A^T on the c2 system (128^3 voxels at 0.1 mm, 128-element cylindrically
+focused array rotated over 180 angles = 23,040 positions, 1024 samples at
+40 MHz, U = 11, dl = U, blob phantom).
+
+One step is one pass of the whole path, s = A x then z = A^T s, over one batch
+of the positions (``--batch-angles`` rotation angles x 128 elements); steps
+walk through the angles.  value = pairs processed / device time, where one A
+or one A^T of a batch processes N x K_batch pairs.  Inputs are resident in HBM
+for ``value``; ``e2e`` repeats the step through the C ABI with x in pinned
+host memory and z copied back.  The L2 is flushed (a 256 MB write) between
+timed steps.
+
+Under torchrun each rank takes its own batches (weak scaling, no data-path
+collective); rank 0 prints one JSON line.  ``--impl reference`` times the FP64
+CPU oracle on the host cores instead, on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2609_29253_gb300 import workloads as W  # noqa: E402
+
+METRIC = "voxel-transducer pairs/s for A and A^T (closed form)"
+N_ANGLES = 180
+# FP32 operations of one quadrant-edge area evaluation of the cylinder path
+# (6-node Gauss-Legendre along v, clamps and branch-point tests; sqrt, asin and
+# reciprocals counted as one operation each), see the roofline section of the
+# design notes.
+FLOPS_PER_QUAD_EVAL = 175
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--batch-angles", type=int, default=4)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sample-voxels", type=int, default=1024)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def batches(args, rank, world, total_steps):
+    """Angle batches for this rank: rank r takes batches r, r + world, ..."""
+    nb = max(1, N_ANGLES // args.batch_angles)
+    out = []
+    for i in range(total_steps):
+        b = (rank + i * world) % nb
+        out.append(np.arange(b * args.batch_angles, (b + 1) * args.batch_angles) * 2 * math.pi / N_ANGLES)
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["clock sampling unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def physical_gpu_index(local):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local < len(ids) and ids[local].isdigit():
+            return int(ids[local])
+    return local
+
+
+def oracle_sample(w, taps, n_vox, seed=0):
+    """Time the FP64 oracle on A and A^T restricted to a seeded voxel subset."""
+    import oracle
+
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(w.N, size=min(n_vox, w.N), replace=False)).astype(np.int64)
+    xs = w.x[idx].astype(np.float64)
+    t0 = time.perf_counter()
+    s, _ = oracle.forward(w, taps, xs, vox_idx=idx)
+    oracle.adjoint(w, taps, s, vox_idx=idx)
+    dt = time.perf_counter() - t0
+    pairs = 2 * idx.size * w.K
+    return pairs / dt, dt, idx.size, oracle.num_threads()
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    ang = batches(args, 0, 1, 1)[0]
+    w = W.c2(angles=ang)
+    taps = oracle.taps_for(w)
+    for _ in range(args.warmup):
+        oracle_sample(w, taps, 64)
+    vals, times = [], []
+    for i in range(args.steps):
+        v, dt, nv, cores = oracle_sample(w, taps, args.cpu_sample_voxels, seed=i)
+        vals.append(v)
+        times.append(dt)
+    value = statistics.mean(vals)
+    sample = (f"{args.cpu_sample_voxels} seeded voxels x {w.K} positions ({args.batch_angles} angles), "
+              f"A then A^T, FP64 oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(args, w),
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config(args, w):
+    return {"workload": "c2: 128^3 voxels @ 0.1 mm, 128-element cylindrical array (R 20 mm, 10 mm elevation, "
+                        "0.3 mm pitch) x 180 angles = 23,040 positions, L 1024 @ 40 MHz, U 11, dl 11, closed form",
+            "batch": f"{args.batch_angles} angles x 128 elements = {128 * args.batch_angles} positions per step",
+            "N": w.N, "K_batch": w.K, "L": w.L, "U": w.U, "dl": w.dl,
+            "l2": "flushed between timed steps (256 MB write)", "parallelism": f"transducer batches over {args.gpus} GPU(s)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2609_29253_gb300 import _lib, api
+
+    total = args.warmup + args.steps
+    angle_sets = batches(args, rank, world, total)
+    w0 = W.c2(angles=angle_sets[0])
+    x = torch.from_numpy(w0.x).to(dev)
+    taps = api.system_taps(w0, dev)
+    plans = []
+    for ang in angle_sets:
+        plans.append(api.Plan(W.c2(angles=ang, with_x=False).with_(x=w0.x), taps=taps, device=dev))
+    K = plans[0].K
+    s = torch.empty((K, w0.L), dtype=torch.float32, device=dev)
+    z = torch.empty(w0.N, dtype=torch.float32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(p):
+        p.forward(x, out=s)
+        p.adjoint(s, out=z)
+
+    for i in range(args.warmup):
+        step(plans[i])
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(physical_gpu_index(local))
+    if rank == 0:
+        clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        p = plans[args.warmup + i]
+        e0, e1, e2 = ev[i]
+        e0.record(stream)
+        p.forward(x, out=s)
+        e1.record(stream)
+        p.adjoint(s, out=z)
+        e2.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop() if rank == 0 else None
+    t_fwd = [a.elapsed_time(b) for a, b, _ in ev]
+    t_adj = [b.elapsed_time(c) for _, b, c in ev]
+    t_step = sum(t_fwd) + sum(t_adj)  # ms, device time of the K steps
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(tt)
+    pairs_step = 2 * w0.N * K
+    value = pairs_step * args.steps * world / (t_step * 1e-3)
+
+    # per-launch work of the dominant kernels (scan counts of the plans)
+    qe = statistics.mean(p.info["quad_evals"] for p in plans[args.warmup:])
+    ae = statistics.mean(p.info["area_evals"] for p in plans[args.warmup:])
+    mean_fwd = statistics.mean(t_fwd) * 1e-3
+    mean_adj = statistics.mean(t_adj) * 1e-3
+    flops = qe * FLOPS_PER_QUAD_EVAL
+    sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the clock seen
+    ach = flops / mean_adj / 1e12
+
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(w0.x).pin_memory()
+        zh = torch.empty(w0.N, dtype=torch.float32).pin_memory()
+        xd = torch.empty_like(x)
+        p = plans[args.warmup]
+        for _ in range(1):
+            xd.copy_(xh, non_blocking=True)
+            p.forward(xd, out=s)
+            p.adjoint(s, out=z)
+            zh.copy_(z, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        ts = []
+        for i in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            xd.copy_(xh, non_blocking=True)
+            plans[args.warmup + i].forward(xd, out=s)
+            plans[args.warmup + i].adjoint(s, out=z)
+            zh.copy_(z, non_blocking=True)
+            torch.cuda.synchronize(dev)
+            ts.append(time.perf_counter() - t0)
+        e2e = {"value": pairs_step * args.steps / sum(ts), "unit": "pairs/s", "h2d_bytes_per_step": 4 * w0.N,
+               "d2h_bytes_per_step": 4 * w0.N}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        wcpu = W.c2(angles=angle_sets[args.warmup], with_x=False).with_(x=w0.x)
+        v, dt, nv, cores = oracle_sample(wcpu, taps, args.cpu_sample_voxels)
+        cpu = {"value": v, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+               "sample": f"{nv} seeded voxels x {wcpu.K} positions, A then A^T, FP64 ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_step / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config(args, w0),
+                "forward_pairs_per_s": w0.N * K / mean_fwd, "adjoint_pairs_per_s": w0.N * K / mean_adj,
+                "area_evals_per_s": ae / mean_adj, "mean_bins_per_pair": plans[args.warmup].info["pair_bins"] / (w0.N * K),
+                "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                             "traffic": None, "kernel": "adj_geom_kernel",
+                             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load"},
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 4 * args.steps,
+                "clocks": clk, "wall_s_timed": t_wall}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

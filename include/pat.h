@@ -1,0 +1,198 @@
+/*
+ * pat.h -- C ABI of the GB300 (sm_103a) library for the matrix-free
+ * photoacoustic operator A and its adjoint A^T (surface method with closed
+ * form areas, and point-detector method), after Do, Escande, Chaux, Gateau and
+ * Lee, "Scalable photoacoustic tomography implementations accounting for the
+ * spatial impulse response of transducers".
+ *
+ * Conventions shared by every entry point
+ *   - SI units.  Voxel i = (iz * ny + iy) * nx + ix sits at
+ *     origin + pitch * (ix, iy, iz) (Sec. 2.4, flattened index).
+ *   - Fine time bins b in [0, U L) are [tau_b, tau_{b+1}) with
+ *     tau_b = t0 + b / (U Fs); the paper's l is b + 1 (Sec. 3.1).
+ *   - Device buffers are borrowed: the caller allocates them (any allocator,
+ *     e.g. PyTorch), keeps them alive until the work queued on `stream` has
+ *     finished, and must not alias an output with an input.  The library
+ *     allocates device memory only inside pat_plan_create (plan constants)
+ *     and frees it in pat_plan_destroy.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Compute entry points only enqueue work; they do not
+ *     synchronise.  An asynchronous kernel fault surfaces as PAT_ERR_CUDA on a
+ *     later call.
+ *   - Every entry point returns a pat_status and never throws;
+ *     pat_last_error() returns a thread-local message for the last failure.
+ *   - Calls on different plans may run concurrently; calls on one plan from
+ *     several host threads must be serialised by the caller.
+ */
+#ifndef PAT_H
+#define PAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pat_status {
+    PAT_OK = 0,
+    PAT_ERR_INVALID_ARG = 1, /* null pointer, bad size or unknown enum */
+    PAT_ERR_GEOMETRY = 2,    /* separation violated: dist_min < kappa (Ass. 1(iii)) or c/(U Fs) > dist_min (Prop. 3) */
+    PAT_ERR_WINDOW = 3,      /* some pair's bins leave [0, U L) and PAT_FLAG_ALLOW_CLIP is not set */
+    PAT_ERR_WORKSPACE = 4,   /* workspace pointer null or smaller than pat_workspace_bytes() */
+    PAT_ERR_CUDA = 5,        /* a CUDA call or kernel launch failed */
+    PAT_ERR_UNSUPPORTED = 6  /* valid request this build does not implement (e.g. shared memory too small) */
+} pat_status;
+
+enum { PAT_PLANE = 0, PAT_CYLINDER = 1 };
+enum { PAT_METHOD_SURFACE = 0, PAT_METHOD_POINT = 1 };
+enum { PAT_RBF_BUMP = 0, PAT_RBF_CONE = 1, PAT_RBF_WENDLAND = 2 };
+enum { PAT_EIR_GAUSS_SINE = 0, PAT_EIR_BOX = 1 };
+enum { PAT_FLAG_ALLOW_CLIP = 1 };
+enum { PAT_OP_FORWARD = 1, PAT_OP_ADJOINT = 2, PAT_OP_RECON = 3 };
+
+/* Uniform voxel grid (Sec. 2.4): centres origin + pitch * (ix, iy, iz). */
+typedef struct pat_grid {
+    int32_t n[3]; /* nx, ny, nz, each >= 1 */
+    int32_t reserved;
+    double origin[3];
+    double pitch; /* > 0 */
+} pat_grid;
+
+/* One transducer position, 16 doubles (the row layout of the Python side).
+ *   plane    (Eq. plane_param):    c0 + x1 e1 + x2 e2, |x1| <= L1, |x2| <= L2;
+ *   cylinder (Eq. cylinder_param): c0 + R cos(t) e2 + R sin(t) (e1 x e2) + z e1,
+ *            |t| <= theta_max < pi/2, |z| <= Lz, c0 on the focal line,
+ *            e1 the cylinder axis.
+ * e1 and e2 must be orthonormal.  kind is PAT_PLANE or PAT_CYLINDER stored as
+ * a double. */
+typedef struct pat_transducer {
+    double kind;
+    double c0[3], e1[3], e2[3];
+    double L1, L2;
+    double R, theta_max, Lz;
+    double reserved;
+} pat_transducer;
+
+/* Time axis and discretisation.  Recording samples l in [0, L) cover
+ * [t0 + l/Fs, t0 + (l+1)/Fs) (Eq. def_operatorS); U is the upsampling factor,
+ * dl the area step of Remark 1 (1 <= dl <= U; dl = 1 is Alg. 3 exactly).
+ * Groups of dl fine bins start at each pair's first bin l_min of
+ * Eq. (rmin_rmax); the last group stops at l_max and its area is split over
+ * its actual length.  method: PAT_METHOD_SURFACE (Alg. 3 + Alg. 4) or
+ * PAT_METHOD_POINT (Alg. 2 with a q1 x q2 midpoint quadrature of each
+ * element, Prop. 2).  flags: PAT_FLAG_ALLOW_CLIP drops fine bins outside
+ * [0, U L) instead of failing plan creation. */
+typedef struct pat_params {
+    double c;  /* speed of sound, > 0 */
+    double fs; /* sampling frequency, > 0 */
+    double t0; /* recording origin, >= 0 */
+    int32_t L, U, dl, method, q1, q2, flags, reserved;
+} pat_params;
+
+/* Radial function and electrical impulse response that define the system
+ * kernel h = e * g with g(t) = -1/2 c t phi(|c t|) (Prop. 1).
+ *   rbf_kind: PAT_RBF_BUMP (1 - r^2/k^2)^2, PAT_RBF_CONE 1 - r/k,
+ *             PAT_RBF_WENDLAND (1 - r/k)^2, all on r < kappa;
+ *   eir_kind: PAT_EIR_GAUSS_SINE exp(-(t-tc)^2/(2 s^2)) sin(2 pi fc (t-tc)) on
+ *             [0, Te], eir = {fc, s, tc, Te};  PAT_EIR_BOX eir[0] on [0, Te],
+ *             eir = {amplitude, -, -, Te}. */
+typedef struct pat_system {
+    int32_t rbf_kind, eir_kind;
+    double kappa;
+    double eir[4];
+} pat_system;
+
+typedef struct pat_plan pat_plan;
+
+typedef struct pat_plan_info {
+    int64_t N, K, L, U, UL, dl, method;
+    int64_t n_taps, n_lo;
+    int64_t bin_lo, bin_hi;   /* extreme fine bins over all pairs (Eq. rmin_rmax) */
+    int64_t area_evals;       /* per application: sum over pairs of ceil(bins / dl) (surface), N K q1 q2 (point) */
+    int64_t pair_bins;        /* sum over pairs of l_max - l_min + 1 */
+    int64_t quad_evals;       /* surface method: sum over pairs of groups x non-degenerate quadrants */
+    int64_t clipped_pairs;    /* pairs with bins outside [0, U L) */
+    int64_t conv_clipped;     /* transducers whose filtered response leaves [0, U L) (dropped by definition) */
+    double dist_min;          /* min over pairs of the distance to the element (Eq. min_dist) */
+    int64_t fwd_blocks, adj_blocks;
+} pat_plan_info;
+
+/* Discrete system kernel (Eq. def_bh):
+ *   h-bar[n] = U Fs int_0^D int_0^D h(t - t' + n D) dt dt',  D = 1/(U Fs),
+ * for n = n_lo .. n_lo + n_taps - 1, computed on the device in FP64 by
+ * composite Gauss-Legendre quadrature split at every kink of e and g.
+ * taps_dev: device array of n_taps doubles (caller-owned, overwritten).
+ * Errors: PAT_ERR_INVALID_ARG for null pointers, n_taps < 1, U < 1, bad kinds
+ * or non-positive c, fs, kappa, Te. */
+pat_status pat_system_kernel(const pat_system *sys, double c, double fs, int32_t U, int32_t n_lo, int32_t n_taps,
+                             double *taps_dev, void *stream);
+
+/* Creates a plan: copies the grid, the K transducer descriptors (host array
+ * tx[K]) and the taps (host array taps_host[n_taps], h-bar[n_lo + t]) to the
+ * device, derives the per-element frames, and scans every voxel-transducer
+ * pair once on the device to find the bin window, the separation dist_min and
+ * the work per application.  kappa is the support radius of the radial
+ * function (Ass. 1).  Synchronises `stream`.  Host arrays are not retained.
+ * Errors: PAT_ERR_INVALID_ARG (null, K < 1, sizes, kinds, dl not in [1, U],
+ * q1/q2 < 1 for the point method, frame not orthonormal, theta_max not in
+ * (0, pi/2)); PAT_ERR_GEOMETRY (separation, Ass. 1(iii) and Prop. 3);
+ * PAT_ERR_WINDOW (bins outside [0, U L) without PAT_FLAG_ALLOW_CLIP);
+ * PAT_ERR_UNSUPPORTED (U L too large for the shared-memory histogram);
+ * PAT_ERR_CUDA.  *out is NULL on failure. */
+pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, const pat_transducer *tx, int32_t K,
+                           const pat_params *params, double kappa, const double *taps_host, int32_t n_taps,
+                           int32_t n_lo, void *stream);
+
+/* Frees the plan's device memory (after synchronising the device). NULL is a no-op. */
+pat_status pat_plan_destroy(pat_plan *plan);
+
+/* Plan facts (see pat_plan_info). */
+pat_status pat_plan_get_info(const pat_plan *plan, pat_plan_info *info);
+
+/* Workspace bytes needed by op (PAT_OP_FORWARD, PAT_OP_ADJOINT, PAT_OP_RECON);
+ * 0 for a null plan or unknown op. */
+size_t pat_workspace_bytes(const pat_plan *plan, int32_t op);
+
+/* s = A x (Alg. 1): x device float[N], s device float[K][L] (overwritten).
+ * Geometric assembly (Alg. 3 / Alg. 2) then convolution with h-bar and
+ * downsampling by U (Eq. discrete_conv).  ws: device workspace of at least
+ * pat_workspace_bytes(plan, PAT_OP_FORWARD) bytes, 256-byte aligned. */
+pat_status pat_forward(pat_plan *plan, const float *x, float *s, void *ws, size_t ws_bytes, void *stream);
+
+/* z = A^T s (Alg. 5): s device float[K][L], z device float[N] (overwritten).
+ * Upsampling transpose, correlation with h-bar^-, then the gather of
+ * Alg. 7 / Alg. 6 (App. G).  ws as for pat_forward with PAT_OP_ADJOINT. */
+pat_status pat_adjoint(pat_plan *plan, const float *s, float *z, void *ws, size_t ws_bytes, void *stream);
+
+/* Stages, for testing and for callers that keep f: */
+/* f = [K][U L] geometric signals (Eq. ui_area with Remark 1 / Eq. def_f_point), overwritten. */
+pat_status pat_forward_geometric(pat_plan *plan, const float *x, float *f, void *ws, size_t ws_bytes, void *stream);
+/* s[K][L] = downsample_U(h-bar * f) (Eq. discrete_conv) from f[K][U L]. */
+pat_status pat_conv_forward(pat_plan *plan, const float *f, float *s, void *stream);
+/* v[K][U L] = h-bar^- * upsample_U^T(s) (App. G) from s[K][L]. */
+pat_status pat_conv_adjoint(pat_plan *plan, const float *s, float *v, void *stream);
+/* z[N] = transpose of the geometric assembly applied to v[K][U L] (Alg. 7 / Alg. 6). */
+pat_status pat_adjoint_geometric(pat_plan *plan, const float *v, float *z, void *ws, size_t ws_bytes, void *stream);
+
+/* Projected FISTA for the Tikhonov non-negative least squares problem of
+ * Eq. (nnls_tik):  min_{p >= 0} 1/2 |A p - s|^2 + 1/2 lambda_R |p|^2.
+ * s device float[K][L]; x device float[N]: initial guess in, solution out.
+ * step <= 0 estimates 1 / |A^T A + lambda_R| by 20 power iterations.
+ * ws: pat_workspace_bytes(plan, PAT_OP_RECON) bytes.  Enqueues 2 operator
+ * applications per iteration; synchronises `stream` only for the step
+ * estimate. */
+pat_status pat_recon(pat_plan *plan, const float *s, float *x, int32_t iters, float lambda_R, float step, void *ws,
+                     size_t ws_bytes, void *stream);
+
+/* Thread-local description of the last failure ("" if none). */
+const char *pat_last_error(void);
+
+/* Library version, e.g. 100 for 0.1.0. */
+int32_t pat_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAT_H */

@@ -1,0 +1,133 @@
+"""Python API over the C ABI: plans, operator calls and autograd.
+
+Tensors are torch CUDA tensors (float32, contiguous).  Workspaces are
+allocated through torch and handed to the library, which allocates nothing per
+call.  Every operator step runs in the CUDA library (``_lib``); nothing here
+computes.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _lib
+from .workloads import Workload
+
+
+def system_taps(w: Workload, device=None) -> np.ndarray:
+    """Discrete system kernel h-bar (Eq. def_bh) computed on the GPU, FP64."""
+    taps = torch.empty(w.T, dtype=torch.float64, device=device or "cuda")
+    _lib.pat_system_kernel(w.rbf_kind, w.kappa, w.eir_kind, w.eir_par, w.c, w.fs, w.U, w.n_lo, taps)
+    return taps.cpu().numpy()
+
+
+class Plan:
+    """An operator A (and A^T) for one grid, one set of transducer positions
+    and one time axis; see pat_plan_create in include/pat.h."""
+
+    def __init__(self, w: Workload, taps: np.ndarray | None = None, allow_clip: bool = False, device=None):
+        self.w = w
+        self.device = torch.device(device or "cuda")
+        with torch.cuda.device(self.device):
+            if taps is None:
+                taps = system_taps(w, self.device)
+            self.taps = np.ascontiguousarray(taps, dtype=np.float64)
+            flags = _lib.PAT_FLAG_ALLOW_CLIP if allow_clip else 0
+            self.handle = _lib.pat_plan_create(w.n, w.origin, w.pitch, w.tx, w.c, w.fs, w.t0, w.L, w.U, w.dl,
+                                               w.method, w.q1, w.q2, flags, w.kappa, self.taps, w.n_lo)
+        self.info = _lib.pat_plan_get_info(self.handle)
+        self._ws = {}
+        self.N, self.K, self.L, self.UL = w.N, w.K, w.L, w.UL
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            _lib.pat_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace(self, op: int) -> torch.Tensor:
+        need = _lib.pat_workspace_bytes(self.handle, op)
+        ws = self._ws.get(op)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
+            self._ws[op] = ws
+        return ws
+
+    def _f32(self, t, n):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous() and t.numel() == n):
+            raise ValueError(f"expected a contiguous float32 CUDA tensor with {n} elements")
+        return t
+
+    def forward(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        x = self._f32(x, self.N)
+        s = out if out is not None else torch.empty((self.K, self.L), dtype=torch.float32, device=self.device)
+        _lib.pat_forward(self.handle, x, s, self.workspace(_lib.PAT_OP_FORWARD))
+        return s
+
+    def adjoint(self, s: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        s = self._f32(s, self.K * self.L)
+        z = out if out is not None else torch.empty(self.N, dtype=torch.float32, device=self.device)
+        _lib.pat_adjoint(self.handle, s, z, self.workspace(_lib.PAT_OP_ADJOINT))
+        return z
+
+    def forward_geometric(self, x: torch.Tensor) -> torch.Tensor:
+        x = self._f32(x, self.N)
+        f = torch.empty((self.K, self.UL), dtype=torch.float32, device=self.device)
+        _lib.pat_forward_geometric(self.handle, x, f, self.workspace(_lib.PAT_OP_FORWARD))
+        return f
+
+    def adjoint_geometric(self, v: torch.Tensor) -> torch.Tensor:
+        v = self._f32(v, self.K * self.UL)
+        z = torch.empty(self.N, dtype=torch.float32, device=self.device)
+        _lib.pat_adjoint_geometric(self.handle, v, z, self.workspace(_lib.PAT_OP_ADJOINT))
+        return z
+
+    def conv_forward(self, f: torch.Tensor) -> torch.Tensor:
+        f = self._f32(f, self.K * self.UL)
+        s = torch.empty((self.K, self.L), dtype=torch.float32, device=self.device)
+        _lib.pat_conv_forward(self.handle, f, s)
+        return s
+
+    def conv_adjoint(self, s: torch.Tensor) -> torch.Tensor:
+        s = self._f32(s, self.K * self.L)
+        v = torch.empty((self.K, self.UL), dtype=torch.float32, device=self.device)
+        _lib.pat_conv_adjoint(self.handle, s, v)
+        return v
+
+    def recon(self, s: torch.Tensor, x0: torch.Tensor | None = None, iters: int = 50, lambda_R: float = 0.0,
+              step: float = 0.0) -> torch.Tensor:
+        """Projected FISTA for Eq. (nnls_tik); step <= 0 estimates 1/|A^T A + lambda|."""
+        s = self._f32(s, self.K * self.L)
+        x = x0.clone() if x0 is not None else torch.zeros(self.N, dtype=torch.float32, device=self.device)
+        _lib.pat_recon(self.handle, s, x, iters, lambda_R, step, self.workspace(_lib.PAT_OP_RECON))
+        return x
+
+
+def plan_from_workload(w: Workload, **kw) -> Plan:
+    return Plan(w, **kw)
+
+
+class PatForward(torch.autograd.Function):
+    """s = A x with backward A^T (the exact transpose, App. G)."""
+
+    @staticmethod
+    def forward(ctx, x, plan):
+        ctx.plan = plan
+        return plan.forward(x.contiguous())
+
+    @staticmethod
+    def backward(ctx, gs):
+        return ctx.plan.adjoint(gs.contiguous()), None
+
+
+def forward(plan: Plan, x: torch.Tensor) -> torch.Tensor:
+    return PatForward.apply(x, plan)
+
+
+def adjoint(plan: Plan, s: torch.Tensor) -> torch.Tensor:
+    return plan.adjoint(s.contiguous())

@@ -1,0 +1,477 @@
+// pat_api.cu -- the C ABI of include/pat.h: plans, validation, workspaces and
+// the enqueueing of the kernels of pat_kernels.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pat.h"
+#include "pat_kernels.cuh"
+
+using namespace pat;
+
+struct pat_plan {
+    int device;
+    int K;
+    long long N;
+    pat_grid grid;
+    pat_params params;
+    double kappa;
+    GridDev g;
+    TimeDev tm;
+    TxDev *tx;
+    double *taps;
+    float *W;
+    int T, nW, n_lo;
+    int fwd_chunks;
+    double *scal; // device scalars for pat_recon
+    pat_plan_info info;
+};
+
+static thread_local std::string g_err;
+
+static pat_status fail(pat_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CK(call)                                                                                                      \
+    do {                                                                                                              \
+        cudaError_t e_ = (call);                                                                                      \
+        if (e_ != cudaSuccess) return fail(PAT_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,  \
+                                           __LINE__);                                                                 \
+    } while (0)
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+extern "C" const char *pat_last_error(void) { return g_err.c_str(); }
+
+extern "C" int32_t pat_version(void) { return 100; }
+
+// ---------------------------------------------------------------------------
+extern "C" pat_status pat_system_kernel(const pat_system *sys, double c, double fs, int32_t U, int32_t n_lo,
+                                        int32_t n_taps, double *taps_dev, void *stream)
+{
+    g_err.clear();
+    if (!sys || !taps_dev) return fail(PAT_ERR_INVALID_ARG, "pat_system_kernel: null pointer");
+    if (n_taps < 1 || U < 1 || !(c > 0) || !(fs > 0) || !(sys->kappa > 0) || !(sys->eir[3] > 0))
+        return fail(PAT_ERR_INVALID_ARG, "pat_system_kernel: sizes and parameters must be positive");
+    if (sys->rbf_kind < PAT_RBF_BUMP || sys->rbf_kind > PAT_RBF_WENDLAND)
+        return fail(PAT_ERR_INVALID_ARG, "pat_system_kernel: unknown rbf_kind %d", sys->rbf_kind);
+    if (sys->eir_kind != PAT_EIR_GAUSS_SINE && sys->eir_kind != PAT_EIR_BOX)
+        return fail(PAT_ERR_INVALID_ARG, "pat_system_kernel: unknown eir_kind %d", sys->eir_kind);
+    if (sys->eir_kind == PAT_EIR_GAUSS_SINE && !(sys->eir[1] > 0))
+        return fail(PAT_ERR_INVALID_ARG, "pat_system_kernel: Gaussian width must be positive");
+    CK(launch_taps(sys->rbf_kind, sys->eir_kind, sys->kappa, c, sys->eir, (double)U * fs, n_lo, n_taps, taps_dev,
+                   (cudaStream_t)stream));
+    return PAT_OK;
+}
+
+// ---------------------------------------------------------------------------
+static pat_status validate(const pat_grid *grid, const pat_transducer *tx, int K, const pat_params *p, double kappa,
+                           const double *taps, int n_taps)
+{
+    if (!grid || !tx || !p || !taps) return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: null pointer");
+    if (K < 1) return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: K must be >= 1");
+    for (int d = 0; d < 3; ++d)
+        if (grid->n[d] < 1) return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: grid size must be >= 1");
+    if (!(grid->pitch > 0)) return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: pitch must be > 0");
+    if (!(p->c > 0) || !(p->fs > 0) || !(p->t0 >= 0))
+        return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: need c > 0, fs > 0, t0 >= 0");
+    if (p->L < 1 || p->U < 1 || p->dl < 1 || p->dl > p->U)
+        return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: need L >= 1, U >= 1, 1 <= dl <= U");
+    if ((long long)p->L * p->U >= (1LL << 30)) return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: U L too large");
+    if (p->method != PAT_METHOD_SURFACE && p->method != PAT_METHOD_POINT)
+        return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: unknown method %d", p->method);
+    if (p->method == PAT_METHOD_POINT && (p->q1 < 1 || p->q2 < 1))
+        return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: point method needs q1, q2 >= 1");
+    if (!(kappa > 0)) return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: kappa must be > 0");
+    if (n_taps < 1) return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: n_taps must be >= 1");
+    for (int k = 0; k < K; ++k) {
+        const pat_transducer &t = tx[k];
+        int kind = (int)t.kind;
+        if ((double)kind != t.kind || (kind != PAT_PLANE && kind != PAT_CYLINDER))
+            return fail(PAT_ERR_INVALID_ARG, "transducer %d: unknown kind %g", k, t.kind);
+        double n1 = t.e1[0] * t.e1[0] + t.e1[1] * t.e1[1] + t.e1[2] * t.e1[2];
+        double n2 = t.e2[0] * t.e2[0] + t.e2[1] * t.e2[1] + t.e2[2] * t.e2[2];
+        double d12 = t.e1[0] * t.e2[0] + t.e1[1] * t.e2[1] + t.e1[2] * t.e2[2];
+        if (fabs(n1 - 1) > 1e-9 || fabs(n2 - 1) > 1e-9 || fabs(d12) > 1e-9)
+            return fail(PAT_ERR_INVALID_ARG, "transducer %d: e1, e2 not orthonormal", k);
+        if (kind == PAT_PLANE && !(t.L1 > 0 && t.L2 > 0))
+            return fail(PAT_ERR_INVALID_ARG, "transducer %d: L1, L2 must be > 0", k);
+        if (kind == PAT_CYLINDER && !(t.R > 0 && t.Lz > 0 && t.theta_max > 0 && t.theta_max < M_PI / 2))
+            return fail(PAT_ERR_INVALID_ARG, "transducer %d: need R > 0, Lz > 0, 0 < theta_max < pi/2", k);
+    }
+    return PAT_OK;
+}
+
+extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, const pat_transducer *tx, int32_t K,
+                                      const pat_params *params, double kappa, const double *taps_host,
+                                      int32_t n_taps, int32_t n_lo, void *stream)
+{
+    g_err.clear();
+    if (!out) return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: null out");
+    *out = nullptr;
+    pat_status st = validate(grid, tx, K, params, kappa, taps_host, n_taps);
+    if (st != PAT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    pat_plan *p = new pat_plan();
+    memset(p, 0, sizeof(*p));
+    CK(cudaGetDevice(&p->device));
+    p->K = K;
+    p->grid = *grid;
+    p->params = *params;
+    p->kappa = kappa;
+    p->N = (long long)grid->n[0] * grid->n[1] * grid->n[2];
+    GridDev &g = p->g;
+    g.nx = grid->n[0];
+    g.ny = grid->n[1];
+    g.nz = grid->n[2];
+    g.nbx = (g.nx + kBrickX - 1) / kBrickX;
+    g.nby = (g.ny + kBrickY - 1) / kBrickY;
+    g.nbz = (g.nz + kBrickZ - 1) / kBrickZ;
+    g.nbricks = (long long)g.nbx * g.nby * g.nbz;
+    TimeDev &tm = p->tm;
+    tm.c = params->c;
+    tm.t0 = params->t0;
+    tm.ufs = (double)params->U * params->fs;
+    tm.r0d = params->c * params->t0;
+    tm.deltad = params->c / tm.ufs;
+    tm.deltaf = (float)tm.deltad;
+    tm.ufsf = (float)tm.ufs;
+    tm.L = params->L;
+    tm.U = params->U;
+    tm.UL = params->L * params->U;
+    tm.dl = params->dl;
+    tm.method = params->method;
+    tm.q1 = params->method == PAT_METHOD_POINT ? params->q1 : 1;
+    tm.q2 = params->method == PAT_METHOD_POINT ? params->q2 : 1;
+
+    int dev = p->device, optin = 0;
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    p->T = n_taps;
+    p->n_lo = n_lo;
+    p->nW = n_taps + params->U - 1;
+    size_t need_fwd = sizeof(float) * (size_t)(tm.UL + 1);
+    size_t need_epi = sizeof(float) * (size_t)(tm.UL + p->nW) + 64;
+    size_t need_adj = sizeof(float) * (size_t)(tm.L + p->nW + tm.UL) + 64;
+    if (need_fwd > (size_t)optin || need_epi > (size_t)optin || need_adj > (size_t)optin) {
+        delete p;
+        return fail(PAT_ERR_UNSUPPORTED, "U L = %d needs %zu bytes of shared memory per block, device has %d", tm.UL,
+                    need_adj, optin);
+    }
+
+    // device constants
+    double *raw = nullptr, *dorig = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(raw);
+        cudaFree(dorig);
+    };
+    if (cudaMalloc(&raw, sizeof(double) * 16 * (size_t)K) != cudaSuccess ||
+        cudaMalloc(&p->tx, sizeof(TxDev) * (size_t)K) != cudaSuccess ||
+        cudaMalloc(&p->taps, sizeof(double) * (size_t)n_taps) != cudaSuccess ||
+        cudaMalloc(&p->W, sizeof(float) * (size_t)p->nW) != cudaSuccess ||
+        cudaMalloc(&p->scal, sizeof(double) * 8) != cudaSuccess) {
+        cleanup();
+        pat_plan_destroy(p);
+        return fail(PAT_ERR_CUDA, "pat_plan_create: cudaMalloc failed");
+    }
+    static_assert(sizeof(pat_transducer) == 16 * sizeof(double), "descriptor layout");
+    pat_status rc = PAT_OK;
+    do {
+        if (cudaMemcpyAsync(raw, tx, sizeof(double) * 16 * (size_t)K, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(p->taps, taps_host, sizeof(double) * (size_t)n_taps, cudaMemcpyHostToDevice, s) !=
+                cudaSuccess) {
+            rc = fail(PAT_ERR_CUDA, "pat_plan_create: copy failed");
+            break;
+        }
+        if (launch_frames(raw, K, grid->origin, grid->pitch, tm.q1, tm.q2, p->tx, s) != cudaSuccess ||
+            launch_combine_taps(p->taps, n_taps, params->U, p->W, s) != cudaSuccess) {
+            rc = fail(PAT_ERR_CUDA, "pat_plan_create: setup kernels failed");
+            break;
+        }
+        // scan every pair once
+        void *sbuf = nullptr;
+        size_t sb = sizeof(long long) * 6 * (size_t)K + 64;
+        if (cudaMalloc(&sbuf, sb) != cudaSuccess) {
+            rc = fail(PAT_ERR_CUDA, "pat_plan_create: cudaMalloc failed");
+            break;
+        }
+        ScanOut so;
+        so.lo = (long long *)sbuf;
+        so.hi = so.lo + K;
+        so.groups = (unsigned long long *)(so.hi + K);
+        so.bins = so.groups + K;
+        so.clipped = so.bins + K;
+        so.quads = so.clipped + K;
+        so.rmin_bits = so.quads + K;
+        std::vector<long long> hb(6 * (size_t)K + 1);
+        cudaError_t e = launch_scan(p->tx, K, tm, g, so, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), sbuf, sizeof(long long) * (6 * (size_t)K + 1),
+                                                  cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(sbuf);
+        if (e != cudaSuccess) {
+            rc = fail(PAT_ERR_CUDA, "pat_plan_create: scan failed: %s", cudaGetErrorString(e));
+            break;
+        }
+        pat_plan_info &in = p->info;
+        in.N = p->N;
+        in.K = K;
+        in.L = tm.L;
+        in.U = tm.U;
+        in.UL = tm.UL;
+        in.dl = tm.dl;
+        in.method = tm.method;
+        in.n_taps = n_taps;
+        in.n_lo = n_lo;
+        in.bin_lo = 0x7fffffffffffffffLL;
+        in.bin_hi = -0x7fffffffffffffffLL;
+        for (int k = 0; k < K; ++k) {
+            long long lo = hb[k], hi = hb[K + k];
+            in.bin_lo = std::min<long long>(in.bin_lo, lo);
+            in.bin_hi = std::max<long long>(in.bin_hi, hi);
+            in.area_evals += hb[2 * (size_t)K + k];
+            in.pair_bins += hb[3 * (size_t)K + k];
+            in.clipped_pairs += hb[4 * (size_t)K + k];
+            in.quad_evals += hb[5 * (size_t)K + k];
+            if (lo + n_lo < 0 || hi + n_lo + n_taps - 1 >= tm.UL) in.conv_clipped++;
+        }
+        unsigned long long rb = (unsigned long long)hb[6 * (size_t)K];
+        memcpy(&in.dist_min, &rb, sizeof(double));
+        // work split of the forward geometric kernel: about 8 CTAs per SM in total
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        long long want = (8LL * std::max(sms, 1) + K - 1) / K;
+        long long maxc = std::max(1LL, g.nbricks / kWarpsPerBlock);
+        p->fwd_chunks = (int)std::max(1LL, std::min(want, maxc));
+        in.fwd_blocks = (long long)p->fwd_chunks * K;
+        in.adj_blocks = (g.nbricks + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        if (!(in.dist_min >= kappa)) {
+            rc = fail(PAT_ERR_GEOMETRY, "dist_min = %.6g m < kappa = %.6g m (Assumption 1(iii))", in.dist_min, kappa);
+            break;
+        }
+        if (!(tm.deltad <= in.dist_min)) {
+            rc = fail(PAT_ERR_GEOMETRY, "c/(U Fs) = %.6g m > dist_min = %.6g m (Prop. 3)", tm.deltad, in.dist_min);
+            break;
+        }
+        if (in.clipped_pairs > 0 && !(params->flags & PAT_FLAG_ALLOW_CLIP)) {
+            rc = fail(PAT_ERR_WINDOW, "%lld pairs have bins outside [0, %d): bins [%lld, %lld]", in.clipped_pairs,
+                      tm.UL, in.bin_lo, in.bin_hi);
+            break;
+        }
+    } while (0);
+    cleanup();
+    if (rc != PAT_OK) {
+        std::string keep = g_err;
+        pat_plan_destroy(p);
+        g_err = keep;
+        return rc;
+    }
+    *out = p;
+    return PAT_OK;
+}
+
+extern "C" pat_status pat_plan_destroy(pat_plan *p)
+{
+    if (!p) return PAT_OK;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    cudaFree(p->tx);
+    cudaFree(p->taps);
+    cudaFree(p->W);
+    cudaFree(p->scal);
+    cudaSetDevice(cur);
+    delete p;
+    return PAT_OK;
+}
+
+extern "C" pat_status pat_plan_get_info(const pat_plan *p, pat_plan_info *info)
+{
+    if (!p || !info) return fail(PAT_ERR_INVALID_ARG, "pat_plan_get_info: null pointer");
+    *info = p->info;
+    return PAT_OK;
+}
+
+static size_t ws_fwd(const pat_plan *p) { return align256(sizeof(float) * (size_t)(p->tm.UL + 1) * p->K); }
+static size_t ws_adj(const pat_plan *p) { return align256(sizeof(float2) * (size_t)(p->tm.UL + 1) * p->K); }
+static size_t ws_recon(const pat_plan *p)
+{
+    return std::max(ws_fwd(p), ws_adj(p)) + align256(sizeof(float) * (size_t)p->K * p->tm.L) +
+           4 * align256(sizeof(float) * (size_t)p->N);
+}
+
+extern "C" size_t pat_workspace_bytes(const pat_plan *p, int32_t op)
+{
+    if (!p) return 0;
+    if (op == PAT_OP_FORWARD) return ws_fwd(p);
+    if (op == PAT_OP_ADJOINT) return ws_adj(p);
+    if (op == PAT_OP_RECON) return ws_recon(p);
+    return 0;
+}
+
+static pat_status check_ws(const pat_plan *p, void *ws, size_t bytes, size_t need, const char *who)
+{
+    if (!ws || bytes < need)
+        return fail(PAT_ERR_WORKSPACE, "%s: workspace %zu bytes at %p, need %zu", who, bytes, ws, need);
+    if (((uintptr_t)ws & 255) != 0) return fail(PAT_ERR_WORKSPACE, "%s: workspace must be 256-byte aligned", who);
+    (void)p;
+    return PAT_OK;
+}
+
+static pat_status enqueue_forward(pat_plan *p, const float *x, float *s, float *f, void *ws, cudaStream_t st)
+{
+    float *D = (float *)ws;
+    CK(launch_fwd_geom(p->tx, p->K, p->tm, p->g, x, D, p->fwd_chunks, st));
+    int mode = p->tm.method == PAT_METHOD_POINT ? 1 : 0;
+    CK(launch_fwd_epilogue(D, p->tm.UL + 1, p->W, p->nW, p->n_lo, p->tm, mode, p->K, s, f, st));
+    return PAT_OK;
+}
+
+static pat_status enqueue_adjoint(pat_plan *p, const float *in, int from_v, float *z, void *ws, cudaStream_t st)
+{
+    int mode = p->tm.method == PAT_METHOD_POINT ? 1 : 0;
+    CK(launch_adj_conv(in, from_v, p->W, p->nW, p->n_lo, p->tm, mode, p->K, ws, st));
+    CK(launch_adj_geom(p->tx, p->K, p->tm, p->g, ws, z, st));
+    return PAT_OK;
+}
+
+extern "C" pat_status pat_forward(pat_plan *p, const float *x, float *s, void *ws, size_t ws_bytes, void *stream)
+{
+    g_err.clear();
+    if (!p || !x || !s) return fail(PAT_ERR_INVALID_ARG, "pat_forward: null pointer");
+    pat_status st = check_ws(p, ws, ws_bytes, ws_fwd(p), "pat_forward");
+    if (st != PAT_OK) return st;
+    return enqueue_forward(p, x, s, nullptr, ws, (cudaStream_t)stream);
+}
+
+extern "C" pat_status pat_forward_geometric(pat_plan *p, const float *x, float *f, void *ws, size_t ws_bytes,
+                                            void *stream)
+{
+    g_err.clear();
+    if (!p || !x || !f) return fail(PAT_ERR_INVALID_ARG, "pat_forward_geometric: null pointer");
+    pat_status st = check_ws(p, ws, ws_bytes, ws_fwd(p), "pat_forward_geometric");
+    if (st != PAT_OK) return st;
+    return enqueue_forward(p, x, nullptr, f, ws, (cudaStream_t)stream);
+}
+
+extern "C" pat_status pat_conv_forward(pat_plan *p, const float *f, float *s, void *stream)
+{
+    g_err.clear();
+    if (!p || !f || !s) return fail(PAT_ERR_INVALID_ARG, "pat_conv_forward: null pointer");
+    CK(launch_fwd_epilogue(f, p->tm.UL, p->W, p->nW, p->n_lo, p->tm, 2, p->K, s, nullptr, (cudaStream_t)stream));
+    return PAT_OK;
+}
+
+extern "C" pat_status pat_conv_adjoint(pat_plan *p, const float *s, float *v, void *stream)
+{
+    g_err.clear();
+    if (!p || !s || !v) return fail(PAT_ERR_INVALID_ARG, "pat_conv_adjoint: null pointer");
+    CK(launch_adj_conv(s, 0, p->W, p->nW, p->n_lo, p->tm, 2, p->K, v, (cudaStream_t)stream));
+    return PAT_OK;
+}
+
+extern "C" pat_status pat_adjoint(pat_plan *p, const float *s, float *z, void *ws, size_t ws_bytes, void *stream)
+{
+    g_err.clear();
+    if (!p || !s || !z) return fail(PAT_ERR_INVALID_ARG, "pat_adjoint: null pointer");
+    pat_status st = check_ws(p, ws, ws_bytes, ws_adj(p), "pat_adjoint");
+    if (st != PAT_OK) return st;
+    return enqueue_adjoint(p, s, 0, z, ws, (cudaStream_t)stream);
+}
+
+extern "C" pat_status pat_adjoint_geometric(pat_plan *p, const float *v, float *z, void *ws, size_t ws_bytes,
+                                            void *stream)
+{
+    g_err.clear();
+    if (!p || !v || !z) return fail(PAT_ERR_INVALID_ARG, "pat_adjoint_geometric: null pointer");
+    pat_status st = check_ws(p, ws, ws_bytes, ws_adj(p), "pat_adjoint_geometric");
+    if (st != PAT_OK) return st;
+    return enqueue_adjoint(p, v, 1, z, ws, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// projected FISTA (Eq. nnls_tik)
+// ---------------------------------------------------------------------------
+extern "C" pat_status pat_recon(pat_plan *p, const float *s, float *x, int32_t iters, float lambda_R, float step,
+                                void *ws, size_t ws_bytes, void *stream)
+{
+    g_err.clear();
+    if (!p || !s || !x) return fail(PAT_ERR_INVALID_ARG, "pat_recon: null pointer");
+    if (iters < 0 || !(lambda_R >= 0)) return fail(PAT_ERR_INVALID_ARG, "pat_recon: need iters >= 0, lambda_R >= 0");
+    pat_status st = check_ws(p, ws, ws_bytes, ws_recon(p), "pat_recon");
+    if (st != PAT_OK) return st;
+    cudaStream_t cs = (cudaStream_t)stream;
+    char *w = (char *)ws;
+    void *opws = w;
+    w += std::max(ws_fwd(p), ws_adj(p));
+    float *r = (float *)w;
+    w += align256(sizeof(float) * (size_t)p->K * p->tm.L);
+    const long long N = p->N, M = (long long)p->K * p->tm.L;
+    float *y = (float *)w;
+    w += align256(sizeof(float) * (size_t)N);
+    float *xo = (float *)w;
+    w += align256(sizeof(float) * (size_t)N);
+    float *g = (float *)w;
+    w += align256(sizeof(float) * (size_t)N);
+    float *v = (float *)w;
+    if (!(step > 0)) {
+        // power iteration on A^T A + lambda I from x (or ones where x vanishes)
+        CK(cudaMemcpyAsync(v, x, sizeof(float) * N, cudaMemcpyDeviceToDevice, cs));
+        CK(launch_dot(v, v, N, p->scal, cs));
+        double nv = 0;
+        CK(cudaMemcpyAsync(&nv, p->scal, sizeof(double), cudaMemcpyDeviceToHost, cs));
+        CK(cudaStreamSynchronize(cs));
+        if (!(nv > 0)) {
+            std::vector<float> ones((size_t)N, 1.f);
+            CK(cudaMemcpyAsync(v, ones.data(), sizeof(float) * N, cudaMemcpyHostToDevice, cs));
+            CK(cudaStreamSynchronize(cs));
+        }
+        CK(launch_dot(v, v, N, p->scal, cs));
+        CK(launch_scale(v, v, N, p->scal, cs));
+        double lam_max = 0;
+        for (int it = 0; it < 20; ++it) {
+            pat_status e = enqueue_forward(p, v, r, nullptr, opws, cs);
+            if (e != PAT_OK) return e;
+            e = enqueue_adjoint(p, r, 0, g, opws, cs);
+            if (e != PAT_OK) return e;
+            CK(launch_dot(g, v, N, p->scal, cs)); // Rayleigh quotient, |v| = 1
+            CK(launch_dot(g, g, N, p->scal + 1, cs));
+            double h[2];
+            CK(cudaMemcpyAsync(h, p->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, cs));
+            CK(cudaStreamSynchronize(cs));
+            lam_max = h[0];
+            if (!(h[1] > 0)) break;
+            CK(launch_scale(g, v, N, p->scal + 1, cs));
+        }
+        double Lc = lam_max + lambda_R;
+        if (!(Lc > 0)) return fail(PAT_ERR_INVALID_ARG, "pat_recon: operator norm estimate is zero");
+        step = (float)(1.0 / (1.05 * Lc));
+    }
+    CK(cudaMemcpyAsync(y, x, sizeof(float) * N, cudaMemcpyDeviceToDevice, cs));
+    CK(cudaMemcpyAsync(xo, x, sizeof(float) * N, cudaMemcpyDeviceToDevice, cs));
+    double t = 1.0;
+    for (int it = 0; it < iters; ++it) {
+        pat_status e = enqueue_forward(p, y, r, nullptr, opws, cs);
+        if (e != PAT_OK) return e;
+        CK(launch_sub(r, s, r, M, cs));
+        e = enqueue_adjoint(p, r, 0, g, opws, cs);
+        if (e != PAT_OK) return e;
+        double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        CK(launch_fista(y, g, xo, N, step, lambda_R, (float)((t - 1.0) / tn), cs));
+        t = tn;
+    }
+    CK(cudaMemcpyAsync(x, xo, sizeof(float) * N, cudaMemcpyDeviceToDevice, cs));
+    return PAT_OK;
+}

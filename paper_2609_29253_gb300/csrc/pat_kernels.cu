@@ -1,0 +1,699 @@
+// pat_kernels.cu -- CUDA kernels of the PAT operator for sm_103a.
+//
+//   frames_kernel        per-element frames (Eq. plane_param, Eq. cylinder_param)
+//   scan_kernel          one pass over all pairs at plan time: bin window,
+//                        separation (Eq. min_dist), work per application
+//   fwd_geom_kernel      geometric assembly of A (Alg. 3 + Alg. 4 / Alg. 2):
+//                        CTA = (voxel chunk, transducer), difference-array
+//                        histogram of f_k in shared memory
+//   fwd_epilogue_kernel  prefix sum, 1/(c tau) weights (Eq. ui_area), then the
+//                        convolution with h-bar and the downsampling by U
+//                        (Eq. discrete_conv) fused, FP64 accumulation
+//   adj_conv_kernel      upsampling transpose + correlation with h-bar^-
+//                        (App. G), weights, and prefix sums for the gather
+//   adj_geom_kernel      gather of Alg. 7 / Alg. 6: CTA = 8 bricks of
+//                        4x4x2 voxels, loop over all transducers, no write
+//                        conflicts (App. G)
+//   taps_kernel          discrete system kernel h-bar (Eq. def_bh), FP64
+#include <cstdio>
+
+#include "pat_geom.cuh"
+#include "pat_kernels.cuh"
+
+namespace pat {
+
+// ---------------------------------------------------------------------------
+// frames
+// ---------------------------------------------------------------------------
+__global__ void frames_kernel(const double *__restrict__ raw, int K, double ox, double oy, double oz, double pitch,
+                              int q1, int q2, TxDev *__restrict__ out)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const double *r = raw + 16 * (size_t)k;
+    const double c0[3] = {r[1], r[2], r[3]}, e1[3] = {r[4], r[5], r[6]}, e2[3] = {r[7], r[8], r[9]};
+    const double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    TxDev t;
+    t.kind = (int)r[0];
+    const double *rows[3];
+    if (t.kind == PAT_PLANE) { // rows e1, e2, e1 x e2
+        rows[0] = e1;
+        rows[1] = e2;
+        rows[2] = n;
+    } else { // rows e2, e1 x e2, e1
+        rows[0] = e2;
+        rows[1] = n;
+        rows[2] = e1;
+    }
+    const double d[3] = {ox - c0[0], oy - c0[1], oz - c0[2]};
+    for (int j = 0; j < 3; ++j) {
+        const double *w = rows[j];
+        t.a0d[j] = w[0] * d[0] + w[1] * d[1] + w[2] * d[2];
+        t.axd[j] = w[0] * pitch;
+        t.ayd[j] = w[1] * pitch;
+        t.azd[j] = w[2] * pitch;
+        t.a0[j] = (float)t.a0d[j];
+        t.ax[j] = (float)t.axd[j];
+        t.ay[j] = (float)t.ayd[j];
+        t.az[j] = (float)t.azd[j];
+    }
+    t.L1d = r[10];
+    t.L2d = r[11];
+    t.Rd = r[12];
+    t.Lzd = r[14];
+    t.cthd = cos(r[13]);
+    t.sthd = sin(r[13]);
+    t.L1 = (float)r[10];
+    t.L2 = (float)r[11];
+    t.R = (float)r[12];
+    t.thmax = (float)r[13];
+    t.Lz = (float)r[14];
+    if (t.kind == PAT_PLANE) t.dq = (float)((2.0 * r[10] / q1) * (2.0 * r[11] / q2));
+    else t.dq = (float)(r[12] * (2.0 * r[13] / q1) * (2.0 * r[14] / q2));
+    t.pad = 0.f;
+    out[k] = t;
+}
+
+// ---------------------------------------------------------------------------
+// plan-time scan of all pairs
+// ---------------------------------------------------------------------------
+__global__ void scan_init_kernel(ScanOut s, int K)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < K) {
+        s.lo[k] = 0x7fffffffffffffffLL;
+        s.hi[k] = -0x7fffffffffffffffLL;
+        s.groups[k] = 0;
+        s.bins[k] = 0;
+        s.clipped[k] = 0;
+        s.quads[k] = 0;
+    }
+    if (k == 0) s.rmin_bits[0] = 0x7ff0000000000000ULL; // +inf
+}
+
+__global__ void scan_kernel(const TxDev *__restrict__ tx, TimeDev tm, GridDev g, int bricks_per_cta, ScanOut s)
+{
+    const int k = blockIdx.y;
+    const TxDev &t = tx[k];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    long long lo = 0x7fffffffffffffffLL, hi = -0x7fffffffffffffffLL;
+    unsigned long long groups = 0, bins = 0, clipped = 0, quads = 0;
+    double rmin = INFINITY;
+    long long b0 = (long long)blockIdx.x * bricks_per_cta;
+    long long b1 = min(b0 + bricks_per_cta, g.nbricks);
+    for (long long br = b0 + warp; br < b1; br += kWarpsPerBlock) {
+        int ix, iy, iz;
+        if (!brick_voxel(g, br, lane, ix, iy, iz)) continue;
+        PairRange pr;
+        pair_range(t, tm, ix, iy, iz, pr);
+        if (pr.bmax < pr.bmin) continue;
+        lo = min(lo, pr.bmin);
+        hi = max(hi, pr.bmax);
+        unsigned long long nb = (unsigned long long)(pr.bmax - pr.bmin + 1);
+        bins += nb;
+        unsigned long long ng = (tm.method == PAT_METHOD_POINT) ? (unsigned long long)tm.q1 * tm.q2 : (nb + tm.dl - 1) / tm.dl;
+        groups += ng;
+        if (tm.method != PAT_METHOD_POINT)
+            quads += ng * (unsigned long long)count_quadrants(t, (float)pr.a1, (float)pr.a2, (float)pr.a3);
+        if (pr.bmin < 0 || pr.bmax >= tm.UL) clipped++;
+        rmin = fmin(rmin, pr.rmin);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        groups += __shfl_xor_sync(0xffffffffu, groups, o);
+        bins += __shfl_xor_sync(0xffffffffu, bins, o);
+        clipped += __shfl_xor_sync(0xffffffffu, clipped, o);
+        quads += __shfl_xor_sync(0xffffffffu, quads, o);
+        rmin = fmin(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+    }
+    if (lane == 0) {
+        atomicMin((long long *)&s.lo[k], lo);
+        atomicMax((long long *)&s.hi[k], hi);
+        atomicAdd(&s.groups[k], groups);
+        atomicAdd(&s.bins[k], bins);
+        atomicAdd(&s.clipped[k], clipped);
+        atomicAdd(&s.quads[k], quads);
+        if (rmin < INFINITY) atomicMin(&s.rmin_bits[0], (unsigned long long)__double_as_longlong(rmin));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// forward geometric assembly
+// ---------------------------------------------------------------------------
+struct FwdSurfaceSink {
+    float *D;
+    int UL;
+    float x, prev;
+    __device__ __forceinline__ int clampi(long long e) const { return (int)(e < 0 ? 0 : (e > UL ? UL : e)); }
+    __device__ __forceinline__ void group(long long e0, long long, float val)
+    {
+        float v = x * val;
+        float dv = v - prev;
+        if (dv != 0.f) atomicAdd(&D[clampi(e0)], dv);
+        prev = v;
+    }
+    __device__ __forceinline__ void finish(long long end)
+    {
+        if (prev != 0.f) atomicAdd(&D[clampi(end)], -prev);
+    }
+};
+
+struct FwdPointSink {
+    float *H;
+    int UL;
+    float x;
+    __device__ __forceinline__ void point(long long b, float w)
+    {
+        if (b >= 0 && b < UL) atomicAdd(&H[b], x * w);
+    }
+};
+
+__global__ void __launch_bounds__(kThreads) fwd_geom_kernel(const TxDev *__restrict__ tx, TimeDev tm, GridDev g,
+                                                            const float *__restrict__ x, float *__restrict__ Dg,
+                                                            int bricks_per_cta)
+{
+    extern __shared__ float sD[];
+    const int k = blockIdx.y;
+    const int n = tm.UL + 1;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) sD[b] = 0.f;
+    __syncthreads();
+    const TxDev &t = tx[k];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    long long b0 = (long long)blockIdx.x * bricks_per_cta;
+    long long b1 = min(b0 + bricks_per_cta, g.nbricks);
+    for (long long br = b0 + warp; br < b1; br += kWarpsPerBlock) {
+        int ix, iy, iz;
+        if (!brick_voxel(g, br, lane, ix, iy, iz)) continue;
+        float xv = x[((long long)iz * g.ny + iy) * g.nx + ix];
+        if (tm.method == PAT_METHOD_POINT) {
+            FwdPointSink s{sD, tm.UL, xv};
+            point_pair(t, tm, ix, iy, iz, s);
+        } else {
+            FwdSurfaceSink s{sD, tm.UL, xv, 0.f};
+            surface_pair(t, tm, ix, iy, iz, s);
+        }
+    }
+    __syncthreads();
+    float *row = Dg + (size_t)k * n;
+    if (gridDim.x == 1) {
+        for (int b = threadIdx.x; b < n; b += blockDim.x) row[b] = sD[b];
+    } else {
+        for (int b = threadIdx.x; b < n; b += blockDim.x) {
+            float v = sD[b];
+            if (v != 0.f) atomicAdd(&row[b], v);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// block-wide exclusive scan of one double per thread (kThreads threads)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double block_exclusive_scan(double v, double *tmp)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        double y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) tmp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        double w = lane < kWarpsPerBlock ? tmp[lane] : 0.0;
+        for (int o = 1; o < 32; o <<= 1) {
+            double y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kWarpsPerBlock) tmp[lane] = w; // inclusive warp totals
+    }
+    __syncthreads();
+    double base = warp > 0 ? tmp[warp - 1] : 0.0;
+    double r = base + inc - v;
+    __syncthreads();
+    return r;
+}
+
+// 1/(c tau_{b+1/2}) times U Fs, in FP64
+__device__ __forceinline__ double bin_weight(const TimeDev &tm, int b)
+{
+    return tm.ufs / (tm.r0d + ((double)b + 0.5) * tm.deltad);
+}
+
+// Convolution with h-bar and downsampling by U (Eq. discrete_conv):
+// s[l] = sum_j W[j] f[U l - n_lo + U - 1 - j], W = box_U * h-bar / U.
+__device__ __forceinline__ void conv_down(const float *f, const float *W, int nW, int n_lo, const TimeDev &tm,
+                                          float *s_out)
+{
+    for (int l = threadIdx.x; l < tm.L; l += blockDim.x) {
+        long long base = (long long)tm.U * l - n_lo + tm.U - 1;
+        int j0 = (int)max(0LL, base - (tm.UL - 1));
+        int j1 = (int)min((long long)nW - 1, base);
+        double acc = 0.0;
+        for (int j = j0; j <= j1; ++j) acc = fma((double)W[j], (double)f[base - j], acc);
+        s_out[l] = (float)acc;
+    }
+}
+
+// mode 0: D (difference array of the surface method) -> f; mode 1: H (point
+// histogram) -> f; mode 2: f given.
+__global__ void __launch_bounds__(kThreads) fwd_epilogue_kernel(const float *__restrict__ in, int in_stride,
+                                                                 const float *__restrict__ Wg, int nW, int n_lo,
+                                                                 TimeDev tm, int mode, float *__restrict__ s,
+                                                                 float *__restrict__ f_out)
+{
+    extern __shared__ float sm[];
+    __shared__ double tmp[kWarpsPerBlock];
+    float *f = sm;            // UL
+    float *W = sm + tm.UL;    // nW
+    const int k = blockIdx.x;
+    const float *row = in + (size_t)k * in_stride;
+    for (int j = threadIdx.x; j < nW; j += blockDim.x) W[j] = Wg[j];
+    const int UL = tm.UL;
+    if (mode == 0) {
+        const int chunk = (UL + blockDim.x - 1) / blockDim.x;
+        const int c0 = min(UL, (int)threadIdx.x * chunk), c1 = min(UL, c0 + chunk);
+        double part = 0.0;
+        for (int b = c0; b < c1; ++b) part += (double)row[b];
+        double run = block_exclusive_scan(part, tmp);
+        for (int b = c0; b < c1; ++b) {
+            run += (double)row[b];
+            f[b] = (float)(run * bin_weight(tm, b));
+        }
+    } else if (mode == 1) {
+        for (int b = threadIdx.x; b < UL; b += blockDim.x) f[b] = (float)((double)row[b] * tm.ufs);
+    } else {
+        for (int b = threadIdx.x; b < UL; b += blockDim.x) f[b] = row[b];
+    }
+    __syncthreads();
+    if (f_out) {
+        float *fo = f_out + (size_t)k * UL;
+        for (int b = threadIdx.x; b < UL; b += blockDim.x) fo[b] = f[b];
+    }
+    if (s) conv_down(f, W, nW, n_lo, tm, s + (size_t)k * tm.L);
+}
+
+// ---------------------------------------------------------------------------
+// adjoint: v = h-bar^- * upsample^T(s); mode 0: P[b] = sum_{b'<b} wgt v (float2
+// hi/lo), mode 1: w = U Fs v (point method), mode 2: v itself.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) adj_conv_kernel(const float *__restrict__ s, int from_v,
+                                                            const float *__restrict__ Wg, int nW, int n_lo,
+                                                            TimeDev tm, int mode, void *__restrict__ out)
+{
+    extern __shared__ float sm[];
+    __shared__ double tmp[kWarpsPerBlock];
+    float *ss = sm;          // L
+    float *W = sm + tm.L;    // nW
+    float *w = W + nW;       // UL (mode 0)
+    const int k = blockIdx.x;
+    const int UL = tm.UL, U = tm.U, L = tm.L;
+    for (int j = threadIdx.x; j < nW; j += blockDim.x) W[j] = Wg[j];
+    if (!from_v)
+        for (int l = threadIdx.x; l < L; l += blockDim.x) ss[l] = s[(size_t)k * L + l];
+    __syncthreads();
+    const long long c0 = U - 1 - n_lo;
+    const int chunk = (UL + blockDim.x - 1) / blockDim.x;
+    const int b0 = min(UL, (int)threadIdx.x * chunk), b1 = min(UL, b0 + chunk);
+    double part = 0.0;
+    for (int b = b0; b < b1; ++b) {
+        // v[b] = sum_l s[l] W[U l + c0 - b], 0 <= U l + c0 - b < nW
+        long long lo = b - c0;
+        int l0 = (int)max(0LL, lo >= 0 ? (lo + U - 1) / U : -((-lo) / U));
+        long long hi = b - c0 + nW - 1;
+        int l1 = (int)min((long long)L - 1, hi >= 0 ? hi / U : -1LL);
+        double acc = 0.0;
+        if (from_v) acc = (double)s[(size_t)k * UL + b]; // v given (stage entry point)
+        else
+            for (int l = l0; l <= l1; ++l) acc = fma((double)ss[l], (double)W[U * l + c0 - b], acc);
+        if (mode == 0) {
+            double wv = acc * bin_weight(tm, b);
+            w[b] = (float)wv;
+            part += (double)w[b];
+        } else if (mode == 1) {
+            ((float *)out)[(size_t)k * (UL + 1) + b] = (float)(acc * tm.ufs);
+        } else {
+            ((float *)out)[(size_t)k * UL + b] = (float)acc;
+        }
+    }
+    if (mode != 0) return;
+    double run = block_exclusive_scan(part, tmp);
+    float2 *P = (float2 *)out + (size_t)k * (UL + 1);
+    for (int b = b0; b < b1; ++b) {
+        float hi = (float)run;
+        P[b] = make_float2(hi, (float)(run - (double)hi));
+        run += (double)w[b];
+    }
+    if (b1 == UL && b0 < b1) {
+        float hi = (float)run;
+        P[UL] = make_float2(hi, (float)(run - (double)hi));
+    }
+    if (UL == 0 && threadIdx.x == 0) P[0] = make_float2(0.f, 0.f);
+}
+
+// ---------------------------------------------------------------------------
+// adjoint gather
+// ---------------------------------------------------------------------------
+struct AdjSurfaceSink {
+    const float2 *__restrict__ P;
+    int UL;
+    float acc;
+    float2 pe;  // P at the current group start
+    bool have;
+    __device__ __forceinline__ int clampi(long long e) const { return (int)(e < 0 ? 0 : (e > UL ? UL : e)); }
+    __device__ __forceinline__ void group(long long e0, long long e1, float val)
+    {
+        if (!have) {
+            pe = __ldg(&P[clampi(e0)]);
+            have = true;
+        }
+        float2 p1 = __ldg(&P[clampi(e1)]);
+        acc = fmaf(val, (p1.x - pe.x) + (p1.y - pe.y), acc);
+        pe = p1;
+    }
+    __device__ __forceinline__ void finish(long long) {}
+};
+
+struct AdjPointSink {
+    const float *__restrict__ w;
+    int UL;
+    float acc;
+    __device__ __forceinline__ void point(long long b, float wt)
+    {
+        if (b >= 0 && b < UL) acc = fmaf(wt, __ldg(&w[b]), acc);
+    }
+};
+
+__global__ void __launch_bounds__(kThreads) adj_geom_kernel(const TxDev *__restrict__ tx, int K, TimeDev tm,
+                                                            GridDev g, const void *__restrict__ Pv,
+                                                            float *__restrict__ z)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long br = (long long)blockIdx.x * kWarpsPerBlock + warp;
+    if (br >= g.nbricks) return;
+    int ix, iy, iz;
+    if (!brick_voxel(g, br, lane, ix, iy, iz)) return;
+    const int stride = tm.UL + 1;
+    double acc = 0.0;
+    for (int k = 0; k < K; ++k) {
+        const TxDev &t = tx[k];
+        if (tm.method == PAT_METHOD_POINT) {
+            AdjPointSink s{(const float *)Pv + (size_t)k * stride, tm.UL, 0.f};
+            point_pair(t, tm, ix, iy, iz, s);
+            acc += (double)s.acc;
+        } else {
+            AdjSurfaceSink s{(const float2 *)Pv + (size_t)k * stride, tm.UL, 0.f, make_float2(0.f, 0.f), false};
+            surface_pair(t, tm, ix, iy, iz, s);
+            acc += (double)s.acc;
+        }
+    }
+    z[((long long)iz * g.ny + iy) * g.nx + ix] = (float)acc;
+}
+
+// ---------------------------------------------------------------------------
+// discrete system kernel (Eq. def_bh) on the device, FP64
+// h-bar[n] = (1/D) int_{-D}^{D} (D - |s|) h(n D + s) ds,  h(t) = int e(t') g(t - t') dt'
+// Composite 16-point Gauss-Legendre, nodes by Newton iteration on P_16.
+// ---------------------------------------------------------------------------
+constexpr int kGL = 16;
+
+struct SysDev {
+    int rbf, eir;
+    double kappa, c;
+    double e[4];
+};
+
+__device__ double rbf_dev(int kind, double kappa, double r)
+{
+    r = fabs(r);
+    if (r >= kappa) return 0.0;
+    double q = r / kappa;
+    if (kind == PAT_RBF_BUMP) return (1.0 - q * q) * (1.0 - q * q);
+    if (kind == PAT_RBF_CONE) return 1.0 - q;
+    return (1.0 - q) * (1.0 - q);
+}
+
+__device__ double eir_dev(const SysDev &sy, double t)
+{
+    if (t < 0.0 || t > sy.e[3]) return 0.0;
+    if (sy.eir == PAT_EIR_GAUSS_SINE) {
+        double d = t - sy.e[2];
+        return exp(-d * d / (2.0 * sy.e[1] * sy.e[1])) * sin(2.0 * 3.141592653589793 * sy.e[0] * d);
+    }
+    return sy.e[0];
+}
+
+__device__ double h_dev(const SysDev &sy, const double *gx, const double *gw, double t)
+{
+    // pieces of [max(0, t - k/c), min(Te, t + k/c)] split at t (kink of g at 0)
+    const double kc = sy.kappa / sy.c;
+    double a = fmax(0.0, t - kc), b = fmin(sy.e[3], t + kc);
+    if (!(b > a)) return 0.0;
+    double cuts[3] = {a, b, b};
+    int nc = 2;
+    if (t > a && t < b) {
+        cuts[1] = t;
+        cuts[2] = b;
+        nc = 3;
+    }
+    double acc = 0.0;
+    const int panels = 4;
+    for (int p = 0; p + 1 < nc; ++p) {
+        double lo = cuts[p], hi = cuts[p + 1], wdt = (hi - lo) / panels;
+        for (int q = 0; q < panels; ++q) {
+            double m = lo + (q + 0.5) * wdt;
+            for (int i = 0; i < kGL; ++i) {
+                double tp = m + 0.5 * wdt * gx[i];
+                double ct = sy.c * (t - tp);
+                acc += 0.5 * wdt * gw[i] * eir_dev(sy, tp) * (-0.5 * ct * rbf_dev(sy.rbf, sy.kappa, ct));
+            }
+        }
+    }
+    return acc;
+}
+
+__global__ void taps_kernel(SysDev sy, double ufs, int n_lo, int T, double *__restrict__ taps)
+{
+    __shared__ double gx[kGL], gw[kGL];
+    if (threadIdx.x < kGL) {
+        int i = threadIdx.x;
+        double x = cos(3.141592653589793 * (i + 0.75) / (kGL + 0.5)), dp = 1.0;
+        for (int it = 0; it < 60; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= kGL; ++k) {
+                double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = kGL * (x * p1 - p0) / (x * x - 1.0);
+            double dx = p1 / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        gx[i] = x;
+        gw[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+    __syncthreads();
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const double D = 1.0 / ufs, kc = sy.kappa / sy.c, Te = sy.e[3];
+    const double nD = (double)(n_lo + t) * D;
+    // breakpoints of the triangle weight (0) and of h (kinks of e and g, shifted)
+    double bp[9];
+    int nb = 0;
+    bp[nb++] = -D;
+    bp[nb++] = 0.0;
+    bp[nb++] = D;
+    const double kinks[6] = {-kc, 0.0, kc, Te - kc, Te, Te + kc};
+    for (int i = 0; i < 6; ++i) {
+        double s = kinks[i] - nD;
+        if (s > -D && s < D && s != 0.0) bp[nb++] = s;
+    }
+    for (int i = 1; i < nb; ++i) // insertion sort
+        for (int j = i; j > 0 && bp[j - 1] > bp[j]; --j) {
+            double tt = bp[j];
+            bp[j] = bp[j - 1];
+            bp[j - 1] = tt;
+        }
+    double acc = 0.0;
+    const int panels = 3;
+    for (int p = 0; p + 1 < nb; ++p) {
+        double lo = bp[p], hi = bp[p + 1];
+        if (!(hi > lo)) continue;
+        double wdt = (hi - lo) / panels;
+        for (int q = 0; q < panels; ++q) {
+            double m = lo + (q + 0.5) * wdt;
+            for (int i = 0; i < kGL; ++i) {
+                double sv = m + 0.5 * wdt * gx[i];
+                acc += 0.5 * wdt * gw[i] * (D - fabs(sv)) * h_dev(sy, gx, gw, nD + sv);
+            }
+        }
+    }
+    taps[t] = acc / D;
+}
+
+// W[j] = (1/U) sum_{u<U} h-bar[n_lo + j - (U-1) + u]: the U-box and h-bar combined
+__global__ void combine_taps_kernel(const double *__restrict__ taps, int T, int U, float *__restrict__ W)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    int nW = T + U - 1;
+    if (j >= nW) return;
+    double acc = 0.0;
+    for (int u = 0; u < U; ++u) {
+        int t = j - (U - 1) + u;
+        if (t >= 0 && t < T) acc += taps[t];
+    }
+    W[j] = (float)(acc / U);
+}
+
+// ---------------------------------------------------------------------------
+// vector kernels for the FISTA loop of pat_recon
+// ---------------------------------------------------------------------------
+__global__ void sub_kernel(const float *__restrict__ a, const float *__restrict__ b, float *__restrict__ o, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        o[i] = a[i] - b[i];
+}
+
+// x_new = max(0, y - step (g + lam y)); y = x_new + mom (x_new - x_old); x_old = x_new
+__global__ void fista_kernel(float *__restrict__ y, const float *__restrict__ g, float *__restrict__ xo, long long n,
+                             float step, float lam, float mom)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float yi = y[i];
+        float xn = fmaxf(0.f, yi - step * (g[i] + lam * yi));
+        float xold = xo[i];
+        xo[i] = xn;
+        y[i] = xn + mom * (xn - xold);
+    }
+}
+
+__global__ void dot_kernel(const float *__restrict__ a, const float *__restrict__ b, long long n,
+                           double *__restrict__ out)
+{
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        acc += (double)a[i] * (double)b[i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
+__global__ void scale_kernel(const float *__restrict__ a, float *__restrict__ o, long long n,
+                             const double *__restrict__ nrm2)
+{
+    float sc = (float)(1.0 / sqrt(fmax(nrm2[0], 1e-300)));
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        o[i] = a[i] * sc;
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+// Dynamic shared memory above 48 KB needs an opt-in per function; set it only
+// when a launch needs more than the default.
+static void set_smem_attr(const void *fn, size_t bytes)
+{
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+cudaError_t launch_frames(const double *raw, int K, const double *origin, double pitch, int q1, int q2, TxDev *out,
+                          cudaStream_t st)
+{
+    frames_kernel<<<(K + 127) / 128, 128, 0, st>>>(raw, K, origin[0], origin[1], origin[2], pitch, q1, q2, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const TxDev *tx, int K, const TimeDev &tm, const GridDev &g, ScanOut s, cudaStream_t st)
+{
+    scan_init_kernel<<<(K + 255) / 256, 256, 0, st>>>(s, K);
+    int bpc = 64;
+    dim3 grid((unsigned)((g.nbricks + bpc - 1) / bpc), (unsigned)K);
+    scan_kernel<<<grid, kThreads, 0, st>>>(tx, tm, g, bpc, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_geom(const TxDev *tx, int K, const TimeDev &tm, const GridDev &g, const float *x, float *Dg,
+                            int chunks, cudaStream_t st)
+{
+    size_t smem = sizeof(float) * (size_t)(tm.UL + 1);
+    set_smem_attr((const void *)fwd_geom_kernel, smem);
+    long long bpc = (g.nbricks + chunks - 1) / chunks;
+    bpc = ((bpc + kWarpsPerBlock - 1) / kWarpsPerBlock) * kWarpsPerBlock;
+    unsigned gx = (unsigned)((g.nbricks + bpc - 1) / bpc);
+    if (gx > 1 && Dg) cudaMemsetAsync(Dg, 0, sizeof(float) * (size_t)(tm.UL + 1) * K, st);
+    fwd_geom_kernel<<<dim3(gx, (unsigned)K), kThreads, smem, st>>>(tx, tm, g, x, Dg, (int)bpc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_epilogue(const float *in, int in_stride, const float *W, int nW, int n_lo, const TimeDev &tm,
+                                int mode, int K, float *s, float *f_out, cudaStream_t st)
+{
+    size_t smem = sizeof(float) * (size_t)(tm.UL + nW);
+    set_smem_attr((const void *)fwd_epilogue_kernel, smem);
+    fwd_epilogue_kernel<<<K, kThreads, smem, st>>>(in, in_stride, W, nW, n_lo, tm, mode, s, f_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_conv(const float *s, int from_v, const float *W, int nW, int n_lo, const TimeDev &tm, int mode,
+                            int K, void *out, cudaStream_t st)
+{
+    size_t smem = sizeof(float) * (size_t)(tm.L + nW + (mode == 0 ? tm.UL : 0));
+    set_smem_attr((const void *)adj_conv_kernel, smem);
+    adj_conv_kernel<<<K, kThreads, smem, st>>>(s, from_v, W, nW, n_lo, tm, mode, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_geom(const TxDev *tx, int K, const TimeDev &tm, const GridDev &g, const void *P, float *z,
+                            cudaStream_t st)
+{
+    unsigned grid = (unsigned)((g.nbricks + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    adj_geom_kernel<<<grid, kThreads, 0, st>>>(tx, K, tm, g, P, z);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_taps(int rbf, int eir, double kappa, double c, const double *e, double ufs, int n_lo, int T,
+                        double *taps, cudaStream_t st)
+{
+    SysDev sy;
+    sy.rbf = rbf;
+    sy.eir = eir;
+    sy.kappa = kappa;
+    sy.c = c;
+    for (int i = 0; i < 4; ++i) sy.e[i] = e[i];
+    taps_kernel<<<(T + 63) / 64, 64, 0, st>>>(sy, ufs, n_lo, T, taps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine_taps(const double *taps, int T, int U, float *W, cudaStream_t st)
+{
+    int nW = T + U - 1;
+    combine_taps_kernel<<<(nW + 255) / 256, 256, 0, st>>>(taps, T, U, W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sub(const float *a, const float *b, float *o, long long n, cudaStream_t st)
+{
+    sub_kernel<<<1216, 256, 0, st>>>(a, b, o, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fista(float *y, const float *g, float *xo, long long n, float step, float lam, float mom,
+                         cudaStream_t st)
+{
+    fista_kernel<<<1216, 256, 0, st>>>(y, g, xo, n, step, lam, mom);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot(const float *a, const float *b, long long n, double *out, cudaStream_t st)
+{
+    cudaMemsetAsync(out, 0, sizeof(double), st);
+    dot_kernel<<<1216, 256, 0, st>>>(a, b, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale(const float *a, float *o, long long n, const double *nrm2, cudaStream_t st)
+{
+    scale_kernel<<<1216, 256, 0, st>>>(a, o, n, nrm2);
+    return cudaGetLastError();
+}
+
+} // namespace pat

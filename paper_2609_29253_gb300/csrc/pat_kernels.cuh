@@ -1,0 +1,37 @@
+// pat_kernels.cuh -- host-side launchers of the PAT kernels (pat_kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pat_internal.cuh"
+
+namespace pat {
+
+// Per-transducer results of the plan-time scan over all pairs.
+struct ScanOut {
+    long long *lo, *hi;                      // extreme fine bins
+    unsigned long long *groups, *bins, *clipped, *quads;
+    unsigned long long *rmin_bits;           // min distance (bits of a positive double)
+};
+
+cudaError_t launch_frames(const double *raw, int K, const double *origin, double pitch, int q1, int q2, TxDev *out,
+                          cudaStream_t st);
+cudaError_t launch_scan(const TxDev *tx, int K, const TimeDev &tm, const GridDev &g, ScanOut s, cudaStream_t st);
+cudaError_t launch_fwd_geom(const TxDev *tx, int K, const TimeDev &tm, const GridDev &g, const float *x, float *Dg,
+                            int chunks, cudaStream_t st);
+cudaError_t launch_fwd_epilogue(const float *in, int in_stride, const float *W, int nW, int n_lo, const TimeDev &tm,
+                                int mode, int K, float *s, float *f_out, cudaStream_t st);
+cudaError_t launch_adj_conv(const float *in, int from_v, const float *W, int nW, int n_lo, const TimeDev &tm, int mode,
+                            int K, void *out, cudaStream_t st);
+cudaError_t launch_adj_geom(const TxDev *tx, int K, const TimeDev &tm, const GridDev &g, const void *P, float *z,
+                            cudaStream_t st);
+cudaError_t launch_taps(int rbf, int eir, double kappa, double c, const double *e, double ufs, int n_lo, int T,
+                        double *taps, cudaStream_t st);
+cudaError_t launch_combine_taps(const double *taps, int T, int U, float *W, cudaStream_t st);
+cudaError_t launch_sub(const float *a, const float *b, float *o, long long n, cudaStream_t st);
+cudaError_t launch_fista(float *y, const float *g, float *xo, long long n, float step, float lam, float mom,
+                         cudaStream_t st);
+cudaError_t launch_dot(const float *a, const float *b, long long n, double *out, cudaStream_t st);
+cudaError_t launch_scale(const float *a, float *o, long long n, const double *nrm2, cudaStream_t st);
+
+} // namespace pat

@@ -1,0 +1,199 @@
+"""GPU parity of the CUDA library against the FP64 oracle, through the C ABI.
+
+Bars (rel L2 = |y - y_ref| / |y_ref| over the whole output):
+  * surface method (closed-form areas), FP32: 1e-5 on s = A x and on
+    z = A^T s, and on every stage (f, conv, correlation, gather);
+  * point method: 5e-5 on s, because FP32 and FP64 distances put a
+    contribution on different sides of a bin edge for a few points
+    (flip-tolerant bound);
+  * system kernel taps (device FP64 quadrature): 1e-12 of max |h-bar|;
+  * dot-product test of the GPU pair (A, A^T): 1e-5.
+Inputs are the seeded workloads; x is rounded to float32 once and the same
+values feed both sides.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2609_29253_gb300 import workloads as W  # noqa: E402
+
+SURF_TOL = 1e-5
+POINT_TOL = 5e-5
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_29253_gb300 import api as A
+
+    return A
+
+
+@pytest.fixture(scope="module")
+def orc(oracle_mod):
+    return oracle_mod
+
+
+def _run(api, orc, w, check_stages=True, tol=SURF_TOL):
+    taps = orc.taps_for(w)
+    plan = api.Plan(w, taps=taps)
+    x32 = w.x.astype(np.float32)
+    xg = torch.from_numpy(x32).cuda()
+    s = plan.forward(xg).cpu().numpy()
+    s_ref, _ = orc.forward(w, taps, x32.astype(np.float64))
+    assert rel(s, s_ref) <= tol, rel(s, s_ref)
+    rng = np.random.default_rng(11)
+    y = rng.standard_normal(s.shape).astype(np.float32)
+    z = plan.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
+    z_ref, _ = orc.adjoint(w, taps, y.astype(np.float64))
+    assert rel(z, z_ref) <= tol, rel(z, z_ref)
+    if check_stages:
+        f = plan.forward_geometric(xg).cpu().numpy()
+        f_ref, _ = orc.geometric_forward(w, x32.astype(np.float64))
+        assert rel(f, f_ref) <= tol, rel(f, f_ref)
+        s2 = plan.conv_forward(torch.from_numpy(f_ref.astype(np.float32)).cuda()).cpu().numpy()
+        s2_ref = orc.conv_forward(w, taps, f_ref.astype(np.float32).astype(np.float64))
+        assert rel(s2, s2_ref) <= 1e-6
+        v = plan.conv_adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
+        v_ref = orc.conv_adjoint(w, taps, y.astype(np.float64))
+        assert rel(v, v_ref) <= 1e-6
+        z2 = plan.adjoint_geometric(torch.from_numpy(v_ref.astype(np.float32)).cuda()).cpu().numpy()
+        z2_ref, _ = orc.geometric_adjoint(w, v_ref.astype(np.float32).astype(np.float64))
+        assert rel(z2, z2_ref) <= tol, rel(z2, z2_ref)
+    return plan, s, s_ref
+
+
+def test_system_kernel_taps(api, orc):
+    for w in (W.c1(), W.c2(n_angles=1, with_x=False)):
+        t = api.system_taps(w)
+        t_ref = orc.taps_for(w)
+        assert np.abs(t - t_ref).max() <= 1e-12 * np.abs(t_ref).max()
+
+
+@pytest.mark.parametrize("dl", [1, 11])
+def test_plane_surface(api, orc, dl):
+    _run(api, orc, W.c1(dl=dl))
+
+
+def test_plane_point(api, orc):
+    _run(api, orc, W.c1(method=W.METHOD_POINT, q=(16, 16)), tol=POINT_TOL)
+
+
+@pytest.mark.parametrize("dl", [1, 11])
+def test_cylinder_surface(api, orc, dl):
+    _run(api, orc, W.small_cylinder(n_vox=12, n_angles=4, n_el=3, dl=dl))
+
+
+def test_cylinder_point(api, orc):
+    w = W.small_cylinder(n_vox=8, n_angles=3, n_el=2)
+    _run(api, orc, w.with_(method=W.METHOD_POINT, q1=16, q2=4), tol=POINT_TOL)
+
+
+def test_ragged_grid_and_many_tiles(api, orc):
+    """Grid sizes that are not multiples of the 4x4x2 brick, several CTAs."""
+    w = W.c1().with_(n=(13, 7, 5), origin=W.centred_origin((13, 7, 5), 0.1e-3))
+    w = w.with_(x=W.uniform_phantom(13 * 7 * 5, 4))
+    _run(api, orc, w)
+    w2 = W.small_cylinder(n_vox=9, n_angles=2, n_el=2).with_(n=(9, 5, 11), origin=W.centred_origin((9, 5, 11), 0.1e-3))
+    w2 = w2.with_(x=W.uniform_phantom(9 * 5 * 11, 5))
+    _run(api, orc, w2)
+
+
+def test_single_voxel_and_single_transducer(api, orc):
+    w = W.c1().with_(n=(1, 1, 1), origin=np.array([0.05e-3, -0.02e-3, 0.01e-3]), x=np.array([0.7], dtype=np.float32))
+    w = w.with_tx(w.tx[:1])
+    _run(api, orc, w)
+
+
+def test_c2_geometry_reduced(api, orc):
+    """The full c2 element and rotation geometry on a coarser grid of the same
+    extent (20^3 voxels over 12.8 mm), 64 positions."""
+    n = 20
+    pitch = 12.8e-3 / n
+    w = W.c2(angles=np.array([0.0, 1.1]), with_x=False)
+    sel = np.arange(0, 256, 4)
+    w = w.with_tx(w.tx[sel]).with_(n=(n, n, n), pitch=pitch, origin=W.centred_origin((n, n, n), pitch))
+    w = w.with_(x=W.blob_phantom(w.n, w.origin, pitch, 40, 0, sigma=(0.4e-3, 1.2e-3)))
+    _run(api, orc, w, check_stages=False)
+
+
+def test_dot_product_gpu(api, orc):
+    w = W.small_cylinder(n_vox=12, n_angles=4, n_el=3)
+    plan = api.Plan(w, taps=orc.taps_for(w))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn(w.N, device="cuda", generator=g)
+    y = torch.randn(w.K, w.L, device="cuda", generator=g)
+    lhs = float((plan.forward(x).double() * y.double()).sum())
+    rhs = float((x.double() * plan.adjoint(y.contiguous()).double()).sum())
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+def test_clipping_matches_oracle(api, orc):
+    """Bins before t0 are dropped on both sides when clipping is allowed."""
+    w = W.c1().with_(t0=6.3e-6, L=200)
+    taps = orc.taps_for(w)
+    from paper_2609_29253_gb300._lib import PatError
+
+    with pytest.raises(PatError, match="PAT_ERR_WINDOW"):
+        api.Plan(w, taps=taps)
+    plan = api.Plan(w, taps=taps, allow_clip=True)
+    assert plan.info["clipped_pairs"] > 0
+    x32 = w.x.astype(np.float32)
+    s = plan.forward(torch.from_numpy(x32).cuda()).cpu().numpy()
+    s_ref, dropped = orc.forward(w, taps, x32.astype(np.float64))
+    assert dropped > 0
+    assert rel(s, s_ref) <= SURF_TOL
+    y = np.random.default_rng(2).standard_normal(s.shape).astype(np.float32)
+    z = plan.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
+    z_ref, _ = orc.adjoint(w, taps, y.astype(np.float64))
+    assert rel(z, z_ref) <= SURF_TOL
+
+
+def test_geometry_error(api, orc):
+    from paper_2609_29253_gb300._lib import PatError
+
+    w = W.c1()
+    tx = w.tx.copy()
+    tx[0, 1:4] = np.array([0.0, 0.0, 0.8e-3])  # element inside the grid
+    with pytest.raises(PatError, match="PAT_ERR_GEOMETRY"):
+        api.Plan(w.with_tx(tx), taps=orc.taps_for(w))
+
+
+def test_autograd_backward_is_adjoint(api, orc):
+    w = W.c1()
+    plan = api.Plan(w, taps=orc.taps_for(w))
+    x = torch.from_numpy(w.x).cuda().requires_grad_(True)
+    s = api.forward(plan, x)
+    g = torch.randn_like(s)
+    (s * g).sum().backward()
+    z = plan.adjoint(g.contiguous())
+    assert torch.allclose(x.grad, z)
+
+
+def test_recon_decreases_objective(api, orc):
+    w = W.c1().with_(n=(8, 8, 8), origin=W.centred_origin((8, 8, 8), 0.1e-3))
+    plan = api.Plan(w, taps=orc.taps_for(w))
+    xt = torch.from_numpy(W.uniform_phantom(512, 7)).cuda()
+    s = plan.forward(xt)
+    lam = 0.0
+
+    def obj(x):
+        r = plan.forward(x) - s
+        return float(0.5 * (r.double() ** 2).sum() + 0.5 * lam * (x.double() ** 2).sum())
+
+    x0 = torch.zeros(512, device="cuda")
+    x5 = plan.recon(s, x0, iters=5, lambda_R=lam)
+    x40 = plan.recon(s, x0, iters=40, lambda_R=lam)
+    assert float(x40.min()) >= 0.0
+    assert obj(x40) < obj(x5) < obj(x0)
