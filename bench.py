@@ -56,6 +56,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-voxels", type=int, default=1024)
+    p.add_argument("--grid", type=int, default=128,
+                   help="voxels per axis over the same 12.8 mm cube (128 = the c2 grid; smaller for profiling)")
     return p.parse_args()
 
 
@@ -157,7 +159,7 @@ def run_reference(args):
 
     oracle.build()
     ang = batches(args, 0, 1, 1)[0]
-    w = W.c2(angles=ang)
+    w = c2w(args, ang)
     taps = oracle.taps_for(w)
     for _ in range(args.warmup):
         oracle_sample(w, taps, 64)
@@ -178,9 +180,22 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def c2w(args, angles, with_x=True):
+    """The c2 workload on a --grid^3 grid over the same 12.8 mm cube."""
+    w = W.c2(angles=angles, with_x=False)
+    if args.grid != 128:
+        n = (args.grid,) * 3
+        pitch = 12.8e-3 / args.grid
+        w = w.with_(n=n, pitch=pitch, origin=W.centred_origin(n, pitch))
+    if with_x:
+        w = w.with_(x=W.blob_phantom(w.n, w.origin, w.pitch, 200, 0))
+    return w
+
+
 def config(args, w):
+    grid = "" if args.grid == 128 else f" [reduced grid {args.grid}^3 for profiling]"
     return {"workload": "c2: 128^3 voxels @ 0.1 mm, 128-element cylindrical array (R 20 mm, 10 mm elevation, "
-                        "0.3 mm pitch) x 180 angles = 23,040 positions, L 1024 @ 40 MHz, U 11, dl 11, closed form",
+                        "0.3 mm pitch) x 180 angles = 23,040 positions, L 1024 @ 40 MHz, U 11, dl 11, closed form" + grid,
             "batch": f"{args.batch_angles} angles x 128 elements = {128 * args.batch_angles} positions per step",
             "N": w.N, "K_batch": w.K, "L": w.L, "U": w.U, "dl": w.dl,
             "l2": "flushed between timed steps (256 MB write)", "parallelism": f"transducer batches over {args.gpus} GPU(s)"}
@@ -204,12 +219,12 @@ def main():
 
     total = args.warmup + args.steps
     angle_sets = batches(args, rank, world, total)
-    w0 = W.c2(angles=angle_sets[0])
+    w0 = c2w(args, angle_sets[0])
     x = torch.from_numpy(w0.x).to(dev)
     taps = api.system_taps(w0, dev)
     plans = []
     for ang in angle_sets:
-        plans.append(api.Plan(W.c2(angles=ang, with_x=False).with_(x=w0.x), taps=taps, device=dev))
+        plans.append(api.Plan(c2w(args, ang, with_x=False).with_(x=w0.x), taps=taps, device=dev))
     K = plans[0].K
     s = torch.empty((K, w0.L), dtype=torch.float32, device=dev)
     z = torch.empty(w0.N, dtype=torch.float32, device=dev)
@@ -297,7 +312,7 @@ def main():
         import oracle
 
         oracle.build()
-        wcpu = W.c2(angles=angle_sets[args.warmup], with_x=False).with_(x=w0.x)
+        wcpu = c2w(args, angle_sets[args.warmup], with_x=False).with_(x=w0.x)
         v, dt, nv, cores = oracle_sample(wcpu, taps, args.cpu_sample_voxels)
         cpu = {"value": v, "unit": "pairs/s", "cores": cores, "kind": "oracle",
                "sample": f"{nv} seeded voxels x {wcpu.K} positions, A then A^T, FP64 ({dt:.1f} s)"}
