@@ -148,6 +148,13 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
     tm.deltad = params->c / tm.ufs;
     tm.deltaf = (float)tm.deltad;
     tm.ufsf = (float)tm.ufs;
+    auto split = [](double v) {
+        float hi = (float)v;
+        return make_float2(hi, (float)(v - (double)hi));
+    };
+    tm.fr0 = split(tm.r0d);
+    tm.fdelta = split(tm.deltad);
+    tm.finvdelta = split(tm.ufs / params->c);
     tm.L = params->L;
     tm.U = params->U;
     tm.UL = params->L * params->U;

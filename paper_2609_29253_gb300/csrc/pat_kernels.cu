@@ -25,6 +25,12 @@ namespace pat {
 // ---------------------------------------------------------------------------
 // frames
 // ---------------------------------------------------------------------------
+__device__ float2 split_ff(double v)
+{
+    float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+
 __global__ void frames_kernel(const double *__restrict__ raw, int K, double ox, double oy, double oz, double pitch,
                               int q1, int q2, TxDev *__restrict__ out)
 {
@@ -68,6 +74,18 @@ __global__ void frames_kernel(const double *__restrict__ raw, int K, double ox, 
     t.R = (float)r[12];
     t.thmax = (float)r[13];
     t.Lz = (float)r[14];
+    for (int j = 0; j < 3; ++j) {
+        t.fa0[j] = split_ff(t.a0d[j]);
+        t.fax[j] = split_ff(t.axd[j]);
+        t.fay[j] = split_ff(t.ayd[j]);
+        t.faz[j] = split_ff(t.azd[j]);
+    }
+    t.fR = split_ff(r[12]);
+    t.fRc = split_ff(r[12] * t.cthd);
+    t.fRs = split_ff(r[12] * t.sthd);
+    t.fL1 = split_ff(r[10]);
+    t.fL2 = split_ff(r[11]);
+    t.fLz = split_ff(r[14]);
     if (t.kind == PAT_PLANE) t.dq = (float)((2.0 * r[10] / q1) * (2.0 * r[11] / q2));
     else t.dq = (float)(r[12] * (2.0 * r[13] / q1) * (2.0 * r[14] / q2));
     t.pad = 0.f;
@@ -107,16 +125,16 @@ __global__ void scan_kernel(const TxDev *__restrict__ tx, TimeDev tm, GridDev g,
         PairRange pr;
         pair_range(t, tm, ix, iy, iz, pr);
         if (pr.bmax < pr.bmin) continue;
-        lo = min(lo, pr.bmin);
-        hi = max(hi, pr.bmax);
+        lo = min(lo, (long long)pr.bmin);
+        hi = max(hi, (long long)pr.bmax);
         unsigned long long nb = (unsigned long long)(pr.bmax - pr.bmin + 1);
         bins += nb;
         unsigned long long ng = (tm.method == PAT_METHOD_POINT) ? (unsigned long long)tm.q1 * tm.q2 : (nb + tm.dl - 1) / tm.dl;
         groups += ng;
         if (tm.method != PAT_METHOD_POINT)
-            quads += ng * (unsigned long long)count_quadrants(t, (float)pr.a1, (float)pr.a2, (float)pr.a3);
+            quads += ng * (unsigned long long)count_quadrants(t, pr.a1, pr.a2, pr.a3);
         if (pr.bmin < 0 || pr.bmax >= tm.UL) clipped++;
-        rmin = fmin(rmin, pr.rmin);
+        rmin = fmin(rmin, (double)pr.rmin);
     }
     for (int o = 16; o > 0; o >>= 1) {
         lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
@@ -145,15 +163,15 @@ struct FwdSurfaceSink {
     float *D;
     int UL;
     float x, prev;
-    __device__ __forceinline__ int clampi(long long e) const { return (int)(e < 0 ? 0 : (e > UL ? UL : e)); }
-    __device__ __forceinline__ void group(long long e0, long long, float val)
+    __device__ __forceinline__ int clampi(int e) const { return min(max(e, 0), UL); }
+    __device__ __forceinline__ void group(int e0, int, float val)
     {
         float v = x * val;
         float dv = v - prev;
         if (dv != 0.f) atomicAdd(&D[clampi(e0)], dv);
         prev = v;
     }
-    __device__ __forceinline__ void finish(long long end)
+    __device__ __forceinline__ void finish(int end)
     {
         if (prev != 0.f) atomicAdd(&D[clampi(end)], -prev);
     }
@@ -163,7 +181,7 @@ struct FwdPointSink {
     float *H;
     int UL;
     float x;
-    __device__ __forceinline__ void point(long long b, float w)
+    __device__ __forceinline__ void point(int b, float w)
     {
         if (b >= 0 && b < UL) atomicAdd(&H[b], x * w);
     }
@@ -174,25 +192,29 @@ __global__ void __launch_bounds__(kThreads) fwd_geom_kernel(const TxDev *__restr
                                                             int bricks_per_cta)
 {
     extern __shared__ float sD[];
+    __shared__ float glx[kGLTable], glw[kGLTable];
     const int k = blockIdx.y;
     const int n = tm.UL + 1;
     for (int b = threadIdx.x; b < n; b += blockDim.x) sD[b] = 0.f;
+    gl_fill(glx, glw, threadIdx.x);
     __syncthreads();
     const TxDev &t = tx[k];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     long long b0 = (long long)blockIdx.x * bricks_per_cta;
     long long b1 = min(b0 + bricks_per_cta, g.nbricks);
-    for (long long br = b0 + warp; br < b1; br += kWarpsPerBlock) {
+    for (long long br = b0 + warp; br < b1; br += kWarpsPerBlock) { // warp-uniform trip count
         int ix, iy, iz;
-        if (!brick_voxel(g, br, lane, ix, iy, iz)) continue;
-        float xv = x[((long long)iz * g.ny + iy) * g.nx + ix];
-        if (tm.method == PAT_METHOD_POINT) {
-            FwdPointSink s{sD, tm.UL, xv};
-            point_pair(t, tm, ix, iy, iz, s);
-        } else {
-            FwdSurfaceSink s{sD, tm.UL, xv, 0.f};
-            surface_pair(t, tm, ix, iy, iz, s);
+        if (brick_voxel(g, br, lane, ix, iy, iz)) {
+            float xv = x[((long long)iz * g.ny + iy) * g.nx + ix];
+            if (tm.method == PAT_METHOD_POINT) {
+                FwdPointSink s{sD, tm.UL, xv};
+                point_pair(t, tm, ix, iy, iz, s);
+            } else {
+                FwdSurfaceSink s{sD, tm.UL, xv, 0.f};
+                surface_pair(t, tm, ix, iy, iz, s, glx, glw);
+            }
         }
+        __syncwarp();
     }
     __syncthreads();
     float *row = Dg + (size_t)k * n;
@@ -360,8 +382,8 @@ struct AdjSurfaceSink {
     float acc;
     float2 pe;  // P at the current group start
     bool have;
-    __device__ __forceinline__ int clampi(long long e) const { return (int)(e < 0 ? 0 : (e > UL ? UL : e)); }
-    __device__ __forceinline__ void group(long long e0, long long e1, float val)
+    __device__ __forceinline__ int clampi(int e) const { return min(max(e, 0), UL); }
+    __device__ __forceinline__ void group(int e0, int e1, float val)
     {
         if (!have) {
             pe = __ldg(&P[clampi(e0)]);
@@ -371,14 +393,14 @@ struct AdjSurfaceSink {
         acc = fmaf(val, (p1.x - pe.x) + (p1.y - pe.y), acc);
         pe = p1;
     }
-    __device__ __forceinline__ void finish(long long) {}
+    __device__ __forceinline__ void finish(int) {}
 };
 
 struct AdjPointSink {
     const float *__restrict__ w;
     int UL;
     float acc;
-    __device__ __forceinline__ void point(long long b, float wt)
+    __device__ __forceinline__ void point(int b, float wt)
     {
         if (b >= 0 && b < UL) acc = fmaf(wt, __ldg(&w[b]), acc);
     }
@@ -388,25 +410,32 @@ __global__ void __launch_bounds__(kThreads) adj_geom_kernel(const TxDev *__restr
                                                             GridDev g, const void *__restrict__ Pv,
                                                             float *__restrict__ z)
 {
+    __shared__ float glx[kGLTable], glw[kGLTable];
+    gl_fill(glx, glw, threadIdx.x);
+    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long br = (long long)blockIdx.x * kWarpsPerBlock + warp;
     if (br >= g.nbricks) return;
     int ix, iy, iz;
-    if (!brick_voxel(g, br, lane, ix, iy, iz)) return;
+    const bool ok = brick_voxel(g, br, lane, ix, iy, iz); // ragged bricks: idle lanes stay for the syncs
     const int stride = tm.UL + 1;
     double acc = 0.0;
     for (int k = 0; k < K; ++k) {
-        const TxDev &t = tx[k];
-        if (tm.method == PAT_METHOD_POINT) {
-            AdjPointSink s{(const float *)Pv + (size_t)k * stride, tm.UL, 0.f};
-            point_pair(t, tm, ix, iy, iz, s);
-            acc += (double)s.acc;
-        } else {
-            AdjSurfaceSink s{(const float2 *)Pv + (size_t)k * stride, tm.UL, 0.f, make_float2(0.f, 0.f), false};
-            surface_pair(t, tm, ix, iy, iz, s);
-            acc += (double)s.acc;
+        if (ok) {
+            const TxDev &t = tx[k];
+            if (tm.method == PAT_METHOD_POINT) {
+                AdjPointSink s{(const float *)Pv + (size_t)k * stride, tm.UL, 0.f};
+                point_pair(t, tm, ix, iy, iz, s);
+                acc += (double)s.acc;
+            } else {
+                AdjSurfaceSink s{(const float2 *)Pv + (size_t)k * stride, tm.UL, 0.f, make_float2(0.f, 0.f), false};
+                surface_pair(t, tm, ix, iy, iz, s, glx, glw);
+                acc += (double)s.acc;
+            }
         }
+        __syncwarp(); // reconverge before the next pair (FP64 setup at full width)
     }
+    if (!ok) return;
     z[((long long)iz * g.ny + iy) * g.nx + ix] = (float)acc;
 }
 
