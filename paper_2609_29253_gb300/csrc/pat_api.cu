@@ -27,6 +27,9 @@ struct pat_plan {
     float *W;
     int T, nW, n_lo;
     int fwd_chunks;
+    int *fwd_base;  // per transducer: first fine-bin edge of its window
+    int fwd_span;   // window length (edges) common to all transducers
+    int smem_optin;
     double *scal; // device scalars for pat_recon
     pat_plan_info info;
 };
@@ -168,10 +171,10 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
     p->T = n_taps;
     p->n_lo = n_lo;
     p->nW = n_taps + params->U - 1;
-    size_t need_fwd = sizeof(float) * (size_t)(tm.UL + 1);
+    p->smem_optin = optin;
     size_t need_epi = sizeof(float) * (size_t)(tm.UL + p->nW) + 64;
     size_t need_adj = sizeof(float) * (size_t)(tm.L + p->nW + tm.UL) + 64;
-    if (need_fwd > (size_t)optin || need_epi > (size_t)optin || need_adj > (size_t)optin) {
+    if (need_epi > (size_t)optin || need_adj > (size_t)optin) {
         delete p;
         return fail(PAT_ERR_UNSUPPORTED, "U L = %d needs %zu bytes of shared memory per block, device has %d", tm.UL,
                     need_adj, optin);
@@ -187,6 +190,7 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
         cudaMalloc(&p->tx, sizeof(TxDev) * (size_t)K) != cudaSuccess ||
         cudaMalloc(&p->taps, sizeof(double) * (size_t)n_taps) != cudaSuccess ||
         cudaMalloc(&p->W, sizeof(float) * (size_t)p->nW) != cudaSuccess ||
+        cudaMalloc(&p->fwd_base, sizeof(int) * (size_t)K) != cudaSuccess ||
         cudaMalloc(&p->scal, sizeof(double) * 8) != cudaSuccess) {
         cleanup();
         pat_plan_destroy(p);
@@ -243,6 +247,33 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
         in.n_lo = n_lo;
         in.bin_lo = 0x7fffffffffffffffLL;
         in.bin_hi = -0x7fffffffffffffffLL;
+        // per-transducer window of the forward difference array: edges of its
+        // pairs lie in [lo, hi + 1]; one bin of margin on either side covers
+        // the point method's FP32 bin decision at the ends of the range
+        std::vector<int> base((size_t)K);
+        long long span = 1;
+        for (int k = 0; k < K; ++k) {
+            long long lo = hb[k], hi = hb[K + k];
+            long long b0 = 0, b1 = 0;
+            if (lo <= hi) {
+                b0 = std::min<long long>(std::max<long long>(lo - 1, 0), tm.UL);
+                b1 = std::max<long long>(std::min<long long>(hi + 2, tm.UL), b0);
+            }
+            base[k] = (int)b0;
+            span = std::max(span, b1 - b0 + 1);
+        }
+        p->fwd_span = (int)span;
+        if (2 * sizeof(float) * (size_t)span > (size_t)p->smem_optin) {
+            rc = fail(PAT_ERR_UNSUPPORTED, "a transducer's bins span %lld fine bins: %zu bytes of shared memory, "
+                      "device has %d", span, 2 * sizeof(float) * (size_t)span, p->smem_optin);
+            break;
+        }
+        if (cudaMemcpyAsync(p->fwd_base, base.data(), sizeof(int) * (size_t)K, cudaMemcpyHostToDevice, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            rc = fail(PAT_ERR_CUDA, "pat_plan_create: copy failed");
+            break;
+        }
         for (int k = 0; k < K; ++k) {
             long long lo = hb[k], hi = hb[K + k];
             in.bin_lo = std::min<long long>(in.bin_lo, lo);
@@ -298,6 +329,7 @@ extern "C" pat_status pat_plan_destroy(pat_plan *p)
     cudaFree(p->tx);
     cudaFree(p->taps);
     cudaFree(p->W);
+    cudaFree(p->fwd_base);
     cudaFree(p->scal);
     cudaSetDevice(cur);
     delete p;
@@ -311,7 +343,7 @@ extern "C" pat_status pat_plan_get_info(const pat_plan *p, pat_plan_info *info)
     return PAT_OK;
 }
 
-static size_t ws_fwd(const pat_plan *p) { return align256(sizeof(float) * (size_t)(p->tm.UL + 1) * p->K); }
+static size_t ws_fwd(const pat_plan *p) { return align256(sizeof(double) * (size_t)(p->tm.UL + 1) * p->K); }
 static size_t ws_adj(const pat_plan *p) { return align256(sizeof(float2) * (size_t)(p->tm.UL + 1) * p->K); }
 static size_t ws_recon(const pat_plan *p)
 {
@@ -339,8 +371,8 @@ static pat_status check_ws(const pat_plan *p, void *ws, size_t bytes, size_t nee
 
 static pat_status enqueue_forward(pat_plan *p, const float *x, float *s, float *f, void *ws, cudaStream_t st)
 {
-    float *D = (float *)ws;
-    CK(launch_fwd_geom(p->tx, p->K, p->tm, p->g, x, D, p->fwd_chunks, st));
+    double *D = (double *)ws;
+    CK(launch_fwd_geom(p->tx, p->K, p->tm, p->g, x, D, p->fwd_chunks, p->fwd_base, p->fwd_span, st));
     int mode = p->tm.method == PAT_METHOD_POINT ? 1 : 0;
     CK(launch_fwd_epilogue(D, p->tm.UL + 1, p->W, p->nW, p->n_lo, p->tm, mode, p->K, s, f, st));
     return PAT_OK;

@@ -159,43 +159,73 @@ __global__ void scan_kernel(const TxDev *__restrict__ tx, TimeDev tm, GridDev g,
 // ---------------------------------------------------------------------------
 // forward geometric assembly
 // ---------------------------------------------------------------------------
+// Compensated accumulation in shared memory: hi[i] takes the FP32 atomic sum,
+// lo[i] the exact rounding error of every addition (recomputed from the value
+// the atomic returns: FP32 atomic addition rounds to nearest even), plus any
+// low part of the addend.  hi + lo then holds the sum to about 2^-44 relative
+// to the partial sums, so the long prefix sum over the difference array does
+// not pile up FP32 rounding.
+__device__ __forceinline__ void acc2(float *hi, float *lo, int i, float v, float vlo)
+{
+    const float old = atomicAdd(&hi[i], v);
+    const float s = old + v;
+    const float bb = s - old;
+    const float err = (old - (s - bb)) + (v - bb);
+    const float l = err + vlo;
+    if (l != 0.f) atomicAdd(&lo[i], l);
+}
+
+// Fine-bin window of one transducer in shared memory: edges base..top.
+struct BinWindow {
+    float *hi, *lo;
+    int base, top;
+    __device__ __forceinline__ int idx(int e) const { return min(max(e, base), top) - base; }
+};
+
 struct FwdSurfaceSink {
-    float *D;
-    int UL;
+    BinWindow w;
     float x, prev;
-    __device__ __forceinline__ int clampi(int e) const { return min(max(e, 0), UL); }
     __device__ __forceinline__ void group(int e0, int, float val)
     {
-        float v = x * val;
-        float dv = v - prev;
-        if (dv != 0.f) atomicAdd(&D[clampi(e0)], dv);
+        const float v = x * val;
+        const float2 dv = ff_two_sum(v, -prev); // exact difference of consecutive group values
+        if (dv.x != 0.f) acc2(w.hi, w.lo, w.idx(e0), dv.x, dv.y);
         prev = v;
     }
     __device__ __forceinline__ void finish(int end)
     {
-        if (prev != 0.f) atomicAdd(&D[clampi(end)], -prev);
+        if (prev != 0.f) acc2(w.hi, w.lo, w.idx(end), -prev, 0.f);
     }
 };
 
 struct FwdPointSink {
-    float *H;
+    BinWindow w;
     int UL;
     float x;
-    __device__ __forceinline__ void point(int b, float w)
+    __device__ __forceinline__ void point(int b, float wt)
     {
-        if (b >= 0 && b < UL) atomicAdd(&H[b], x * w);
+        if (b >= w.base && b <= w.top && b < UL) acc2(w.hi, w.lo, b - w.base, x * wt, 0.f);
     }
 };
 
+// base[k]: first fine-bin edge of transducer k's window (from the plan-time
+// scan); span: window length shared by all k.  Dg: [K][UL + 1] doubles, zeroed
+// by the launcher; each CTA adds its window into row k.
 __global__ void __launch_bounds__(kThreads) fwd_geom_kernel(const TxDev *__restrict__ tx, TimeDev tm, GridDev g,
-                                                            const float *__restrict__ x, float *__restrict__ Dg,
-                                                            int bricks_per_cta)
+                                                            const float *__restrict__ x, double *__restrict__ Dg,
+                                                            int bricks_per_cta, const int *__restrict__ base,
+                                                            int span)
 {
     extern __shared__ float sD[];
     __shared__ float glx[kGLTable], glw[kGLTable];
     const int k = blockIdx.y;
     const int n = tm.UL + 1;
-    for (int b = threadIdx.x; b < n; b += blockDim.x) sD[b] = 0.f;
+    BinWindow win;
+    win.hi = sD;
+    win.lo = sD + span;
+    win.base = base[k];
+    win.top = min(tm.UL, win.base + span - 1);
+    for (int b = threadIdx.x; b < 2 * span; b += blockDim.x) sD[b] = 0.f;
     gl_fill(glx, glw, threadIdx.x);
     __syncthreads();
     const TxDev &t = tx[k];
@@ -207,23 +237,24 @@ __global__ void __launch_bounds__(kThreads) fwd_geom_kernel(const TxDev *__restr
         if (brick_voxel(g, br, lane, ix, iy, iz)) {
             float xv = x[((long long)iz * g.ny + iy) * g.nx + ix];
             if (tm.method == PAT_METHOD_POINT) {
-                FwdPointSink s{sD, tm.UL, xv};
+                FwdPointSink s{win, tm.UL, xv};
                 point_pair(t, tm, ix, iy, iz, s);
             } else {
-                FwdSurfaceSink s{sD, tm.UL, xv, 0.f};
+                FwdSurfaceSink s{win, xv, 0.f};
                 surface_pair(t, tm, ix, iy, iz, s, glx, glw);
             }
         }
         __syncwarp();
     }
     __syncthreads();
-    float *row = Dg + (size_t)k * n;
+    double *row = Dg + (size_t)k * n + win.base;
+    const int m = win.top - win.base + 1;
     if (gridDim.x == 1) {
-        for (int b = threadIdx.x; b < n; b += blockDim.x) row[b] = sD[b];
+        for (int i = threadIdx.x; i < m; i += blockDim.x) row[i] = (double)win.hi[i] + (double)win.lo[i];
     } else {
-        for (int b = threadIdx.x; b < n; b += blockDim.x) {
-            float v = sD[b];
-            if (v != 0.f) atomicAdd(&row[b], v);
+        for (int i = threadIdx.x; i < m; i += blockDim.x) {
+            const double v = (double)win.hi[i] + (double)win.lo[i];
+            if (v != 0.0) atomicAdd(&row[i], v);
         }
     }
 }
@@ -277,9 +308,9 @@ __device__ __forceinline__ void conv_down(const float *f, const float *W, int nW
     }
 }
 
-// mode 0: D (difference array of the surface method) -> f; mode 1: H (point
-// histogram) -> f; mode 2: f given.
-__global__ void __launch_bounds__(kThreads) fwd_epilogue_kernel(const float *__restrict__ in, int in_stride,
+// mode 0: D (difference array of the surface method, doubles) -> f; mode 1:
+// H (point histogram, doubles) -> f; mode 2: f given (floats).
+__global__ void __launch_bounds__(kThreads) fwd_epilogue_kernel(const void *__restrict__ in, int in_stride,
                                                                  const float *__restrict__ Wg, int nW, int n_lo,
                                                                  TimeDev tm, int mode, float *__restrict__ s,
                                                                  float *__restrict__ f_out)
@@ -289,21 +320,22 @@ __global__ void __launch_bounds__(kThreads) fwd_epilogue_kernel(const float *__r
     float *f = sm;            // UL
     float *W = sm + tm.UL;    // nW
     const int k = blockIdx.x;
-    const float *row = in + (size_t)k * in_stride;
+    const double *drow = (const double *)in + (size_t)k * in_stride;
+    const float *row = (const float *)in + (size_t)k * in_stride;
     for (int j = threadIdx.x; j < nW; j += blockDim.x) W[j] = Wg[j];
     const int UL = tm.UL;
     if (mode == 0) {
         const int chunk = (UL + blockDim.x - 1) / blockDim.x;
         const int c0 = min(UL, (int)threadIdx.x * chunk), c1 = min(UL, c0 + chunk);
         double part = 0.0;
-        for (int b = c0; b < c1; ++b) part += (double)row[b];
+        for (int b = c0; b < c1; ++b) part += drow[b];
         double run = block_exclusive_scan(part, tmp);
         for (int b = c0; b < c1; ++b) {
-            run += (double)row[b];
+            run += drow[b];
             f[b] = (float)(run * bin_weight(tm, b));
         }
     } else if (mode == 1) {
-        for (int b = threadIdx.x; b < UL; b += blockDim.x) f[b] = (float)((double)row[b] * tm.ufs);
+        for (int b = threadIdx.x; b < UL; b += blockDim.x) f[b] = (float)(drow[b] * tm.ufs);
     } else {
         for (int b = threadIdx.x; b < UL; b += blockDim.x) f[b] = row[b];
     }
@@ -640,20 +672,21 @@ cudaError_t launch_scan(const TxDev *tx, int K, const TimeDev &tm, const GridDev
     return cudaGetLastError();
 }
 
-cudaError_t launch_fwd_geom(const TxDev *tx, int K, const TimeDev &tm, const GridDev &g, const float *x, float *Dg,
-                            int chunks, cudaStream_t st)
+cudaError_t launch_fwd_geom(const TxDev *tx, int K, const TimeDev &tm, const GridDev &g, const float *x, double *Dg,
+                            int chunks, const int *base, int span, cudaStream_t st)
 {
-    size_t smem = sizeof(float) * (size_t)(tm.UL + 1);
+    size_t smem = 2 * sizeof(float) * (size_t)span;
     set_smem_attr((const void *)fwd_geom_kernel, smem);
     long long bpc = (g.nbricks + chunks - 1) / chunks;
     bpc = ((bpc + kWarpsPerBlock - 1) / kWarpsPerBlock) * kWarpsPerBlock;
     unsigned gx = (unsigned)((g.nbricks + bpc - 1) / bpc);
-    if (gx > 1 && Dg) cudaMemsetAsync(Dg, 0, sizeof(float) * (size_t)(tm.UL + 1) * K, st);
-    fwd_geom_kernel<<<dim3(gx, (unsigned)K), kThreads, smem, st>>>(tx, tm, g, x, Dg, (int)bpc);
+    cudaError_t e = cudaMemsetAsync(Dg, 0, sizeof(double) * (size_t)(tm.UL + 1) * K, st);
+    if (e != cudaSuccess) return e;
+    fwd_geom_kernel<<<dim3(gx, (unsigned)K), kThreads, smem, st>>>(tx, tm, g, x, Dg, (int)bpc, base, span);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fwd_epilogue(const float *in, int in_stride, const float *W, int nW, int n_lo, const TimeDev &tm,
+cudaError_t launch_fwd_epilogue(const void *in, int in_stride, const float *W, int nW, int n_lo, const TimeDev &tm,
                                 int mode, int K, float *s, float *f_out, cudaStream_t st)
 {
     size_t smem = sizeof(float) * (size_t)(tm.UL + nW);

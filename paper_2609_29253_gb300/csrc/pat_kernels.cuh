@@ -17,9 +17,11 @@ struct ScanOut {
 cudaError_t launch_frames(const double *raw, int K, const double *origin, double pitch, int q1, int q2, TxDev *out,
                           cudaStream_t st);
 cudaError_t launch_scan(const TxDev *tx, int K, const TimeDev &tm, const GridDev &g, ScanOut s, cudaStream_t st);
-cudaError_t launch_fwd_geom(const TxDev *tx, int K, const TimeDev &tm, const GridDev &g, const float *x, float *Dg,
-                            int chunks, cudaStream_t st);
-cudaError_t launch_fwd_epilogue(const float *in, int in_stride, const float *W, int nW, int n_lo, const TimeDev &tm,
+// Dg: [K][UL + 1] doubles; base[k], span: fine-bin window of each transducer.
+cudaError_t launch_fwd_geom(const TxDev *tx, int K, const TimeDev &tm, const GridDev &g, const float *x, double *Dg,
+                            int chunks, const int *base, int span, cudaStream_t st);
+// in: doubles for mode 0 / 1 (difference array, histogram), floats for mode 2 (f)
+cudaError_t launch_fwd_epilogue(const void *in, int in_stride, const float *W, int nW, int n_lo, const TimeDev &tm,
                                 int mode, int K, float *s, float *f_out, cudaStream_t st);
 cudaError_t launch_adj_conv(const float *in, int from_v, const float *W, int nW, int n_lo, const TimeDev &tm, int mode,
                             int K, void *out, cudaStream_t st);
