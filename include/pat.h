@@ -185,6 +185,25 @@ pat_status pat_adjoint_geometric(pat_plan *plan, const float *v, float *z, void 
 pat_status pat_recon(pat_plan *plan, const float *s, float *x, int32_t iters, float lambda_R, float step, void *ws,
                      size_t ws_bytes, void *stream);
 
+/* s = A x like pat_forward, for callers that cannot allocate device memory
+ * (for example code running where cudaMalloc is forbidden or unavailable,
+ * such as inside a host callback or a plug-in that must not touch the
+ * allocator).  There is no counterpart in the paper: it is a deployment
+ * variant of pat_forward.  The forward workspace comes from a fixed scratch
+ * array of PAT_STATIC_SCRATCH_BYTES (16 MiB) that the library places in
+ * device memory at module load; every GPU that loads the library keeps it
+ * until the process exits.  Plans whose pat_workspace_bytes(plan,
+ * PAT_OP_FORWARD) exceeds that size are rejected with PAT_ERR_WORKSPACE.
+ * The first call on each device looks the array up (cudaGetSymbolAddress
+ * with that device current); make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's contents (each
+ * call clears what must start at zero), so calls that overlap on the GPU
+ * (different streams, or different host threads) race: serialise them.  The
+ * call allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * routine. */
+#define PAT_STATIC_SCRATCH_BYTES (16u << 20)
+pat_status pat_forward_static(pat_plan *plan, const float *x, float *s, void *stream);
+
 /* Thread-local description of the last failure ("" if none). */
 const char *pat_last_error(void);
 

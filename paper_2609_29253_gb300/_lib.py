@@ -16,6 +16,7 @@ import numpy as np
 from . import build as _build
 
 PAT_OK = 0
+PAT_ERR_WORKSPACE = 4
 PAT_OP_FORWARD, PAT_OP_ADJOINT, PAT_OP_RECON = 1, 2, 3
 PAT_FLAG_ALLOW_CLIP = 1
 _STATUS = {0: "PAT_OK", 1: "PAT_ERR_INVALID_ARG", 2: "PAT_ERR_GEOMETRY", 3: "PAT_ERR_WINDOW",
@@ -51,7 +52,7 @@ class pat_plan_info(C.Structure):
 
 EXPORTS = ["pat_system_kernel", "pat_plan_create", "pat_plan_destroy", "pat_plan_get_info", "pat_workspace_bytes",
            "pat_forward", "pat_adjoint", "pat_forward_geometric", "pat_conv_forward", "pat_conv_adjoint",
-           "pat_adjoint_geometric", "pat_recon", "pat_last_error", "pat_version"]
+           "pat_adjoint_geometric", "pat_recon", "pat_forward_static", "pat_last_error", "pat_version"]
 
 _lock = threading.Lock()
 _lib = None
@@ -90,6 +91,8 @@ def load(build_if_missing: bool = True):
         for nm in ("pat_conv_forward", "pat_conv_adjoint"):
             getattr(L, nm).restype = st
             getattr(L, nm).argtypes = [vp, vp, vp, vp]
+        L.pat_forward_static.restype = st
+        L.pat_forward_static.argtypes = [vp, vp, vp, vp]
         L.pat_recon.restype = st
         L.pat_recon.argtypes = [vp, vp, vp, C.c_int32, C.c_float, C.c_float, vp, C.c_size_t, vp]
         L.pat_last_error.restype = C.c_char_p
@@ -182,6 +185,10 @@ def pat_conv_adjoint(plan, s, v, stream=None):
 def pat_recon(plan, s, x, iters, lambda_R, step, ws, stream=None):
     check(load().pat_recon(plan, _ptr(s), _ptr(x), int(iters), float(lambda_R), float(step), _ptr(ws), ws.numel(),
                            _stream(stream)))
+
+
+def pat_forward_static(plan, x, s, stream=None):
+    check(load().pat_forward_static(plan, _ptr(x), _ptr(s), _stream(stream)))
 
 
 def pat_version():

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -513,4 +514,41 @@ extern "C" pat_status pat_recon(pat_plan *p, const float *s, float *x, int32_t i
     }
     CK(cudaMemcpyAsync(x, xo, sizeof(float) * N, cudaMemcpyDeviceToDevice, cs));
     return PAT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Forward operator with fixed scratch, for callers that cannot allocate.
+// ---------------------------------------------------------------------------
+// In host code g_static_scratch names a host-side stand-in, not device memory:
+// only the address returned by cudaGetSymbolAddress may reach a kernel.
+static __device__ __align__(256) unsigned char g_static_scratch[PAT_STATIC_SCRATCH_BYTES];
+
+static std::mutex g_static_mu;
+static void *g_static_ptr[256]; // per device, filled on the first call there
+
+extern "C" pat_status pat_forward_static(pat_plan *p, const float *x, float *s, void *stream)
+{
+    g_err.clear();
+    if (!p || !x || !s) return fail(PAT_ERR_INVALID_ARG, "pat_forward_static: null pointer");
+    const size_t need = ws_fwd(p);
+    if (need > (size_t)PAT_STATIC_SCRATCH_BYTES)
+        return fail(PAT_ERR_WORKSPACE,
+                    "pat_forward_static: this plan needs %zu bytes of scratch, the fixed array holds %u "
+                    "(K (U L + 1) 8 bytes must fit; use pat_forward with a caller workspace)",
+                    need, (unsigned)PAT_STATIC_SCRATCH_BYTES);
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev != p->device) return fail(PAT_ERR_INVALID_ARG, "pat_forward_static: plan belongs to device %d", p->device);
+    if (dev < 0 || dev >= 256) return fail(PAT_ERR_UNSUPPORTED, "pat_forward_static: device index %d", dev);
+    void *ptr = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        if (!g_static_ptr[dev]) {
+            void *q = nullptr;
+            CK(cudaGetSymbolAddress(&q, g_static_scratch));
+            g_static_ptr[dev] = q;
+        }
+        ptr = g_static_ptr[dev];
+    }
+    return enqueue_forward(p, x, s, nullptr, ptr, (cudaStream_t)stream);
 }
