@@ -31,6 +31,7 @@ struct pat_plan {
     int *fwd_base;  // per transducer: first fine-bin edge of its window
     int fwd_span;   // window length (edges) common to all transducers
     int smem_optin;
+    int kind_all;   // PAT_PLANE / PAT_CYLINDER if every element has it, else kKindAny
     double *scal; // device scalars for pat_recon
     pat_plan_info info;
 };
@@ -136,6 +137,9 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
     p->params = *params;
     p->kappa = kappa;
     p->N = (long long)grid->n[0] * grid->n[1] * grid->n[2];
+    p->kind_all = (int)tx[0].kind;
+    for (int k = 1; k < K; ++k)
+        if ((int)tx[k].kind != p->kind_all) p->kind_all = kKindAny;
     GridDev &g = p->g;
     g.nx = grid->n[0];
     g.ny = grid->n[1];
@@ -373,7 +377,7 @@ static pat_status check_ws(const pat_plan *p, void *ws, size_t bytes, size_t nee
 static pat_status enqueue_forward(pat_plan *p, const float *x, float *s, float *f, void *ws, cudaStream_t st)
 {
     double *D = (double *)ws;
-    CK(launch_fwd_geom(p->tx, p->K, p->tm, p->g, x, D, p->fwd_chunks, p->fwd_base, p->fwd_span, st));
+    CK(launch_fwd_geom(p->tx, p->K, p->kind_all, p->tm, p->g, x, D, p->fwd_chunks, p->fwd_base, p->fwd_span, st));
     int mode = p->tm.method == PAT_METHOD_POINT ? 1 : 0;
     CK(launch_fwd_epilogue(D, p->tm.UL + 1, p->W, p->nW, p->n_lo, p->tm, mode, p->K, s, f, st));
     return PAT_OK;
@@ -383,7 +387,7 @@ static pat_status enqueue_adjoint(pat_plan *p, const float *in, int from_v, floa
 {
     int mode = p->tm.method == PAT_METHOD_POINT ? 1 : 0;
     CK(launch_adj_conv(in, from_v, p->W, p->nW, p->n_lo, p->tm, mode, p->K, ws, st));
-    CK(launch_adj_geom(p->tx, p->K, p->tm, p->g, ws, z, st));
+    CK(launch_adj_geom(p->tx, p->K, p->kind_all, p->tm, p->g, ws, z, st));
     return PAT_OK;
 }
 

@@ -211,7 +211,8 @@ struct FwdPointSink {
 // base[k]: first fine-bin edge of transducer k's window (from the plan-time
 // scan); span: window length shared by all k.  Dg: [K][UL + 1] doubles, zeroed
 // by the launcher; each CTA adds its window into row k.
-__global__ void __launch_bounds__(kThreads) fwd_geom_kernel(const TxDev *__restrict__ tx, TimeDev tm, GridDev g,
+template <int METHOD, int KIND>
+__global__ void __launch_bounds__(kThreads, 4) fwd_geom_kernel(const TxDev *__restrict__ tx, TimeDev tm, GridDev g,
                                                             const float *__restrict__ x, double *__restrict__ Dg,
                                                             int bricks_per_cta, const int *__restrict__ base,
                                                             int span)
@@ -236,12 +237,12 @@ __global__ void __launch_bounds__(kThreads) fwd_geom_kernel(const TxDev *__restr
         int ix, iy, iz;
         if (brick_voxel(g, br, lane, ix, iy, iz)) {
             float xv = x[((long long)iz * g.ny + iy) * g.nx + ix];
-            if (tm.method == PAT_METHOD_POINT) {
+            if (METHOD == PAT_METHOD_POINT) {
                 FwdPointSink s{win, tm.UL, xv};
-                point_pair(t, tm, ix, iy, iz, s);
+                point_pair<KIND>(t, tm, ix, iy, iz, s);
             } else {
                 FwdSurfaceSink s{win, xv, 0.f};
-                surface_pair(t, tm, ix, iy, iz, s, glx, glw);
+                surface_pair<KIND>(t, tm, ix, iy, iz, s, glx, glw);
             }
         }
         __syncwarp();
@@ -438,7 +439,8 @@ struct AdjPointSink {
     }
 };
 
-__global__ void __launch_bounds__(kThreads) adj_geom_kernel(const TxDev *__restrict__ tx, int K, TimeDev tm,
+template <int METHOD, int KIND>
+__global__ void __launch_bounds__(kThreads, 4) adj_geom_kernel(const TxDev *__restrict__ tx, int K, TimeDev tm,
                                                             GridDev g, const void *__restrict__ Pv,
                                                             float *__restrict__ z)
 {
@@ -455,13 +457,13 @@ __global__ void __launch_bounds__(kThreads) adj_geom_kernel(const TxDev *__restr
     for (int k = 0; k < K; ++k) {
         if (ok) {
             const TxDev &t = tx[k];
-            if (tm.method == PAT_METHOD_POINT) {
+            if (METHOD == PAT_METHOD_POINT) {
                 AdjPointSink s{(const float *)Pv + (size_t)k * stride, tm.UL, 0.f};
-                point_pair(t, tm, ix, iy, iz, s);
+                point_pair<KIND>(t, tm, ix, iy, iz, s);
                 acc += (double)s.acc;
             } else {
                 AdjSurfaceSink s{(const float2 *)Pv + (size_t)k * stride, tm.UL, 0.f, make_float2(0.f, 0.f), false};
-                surface_pair(t, tm, ix, iy, iz, s, glx, glw);
+                surface_pair<KIND>(t, tm, ix, iy, iz, s, glx, glw);
                 acc += (double)s.acc;
             }
         }
@@ -672,18 +674,38 @@ cudaError_t launch_scan(const TxDev *tx, int K, const TimeDev &tm, const GridDev
     return cudaGetLastError();
 }
 
-cudaError_t launch_fwd_geom(const TxDev *tx, int K, const TimeDev &tm, const GridDev &g, const float *x, double *Dg,
-                            int chunks, const int *base, int span, cudaStream_t st)
+// One instantiation per (method, element kind); kind kKindAny reads it from
+// each descriptor.
+template <int METHOD, int KIND>
+static cudaError_t fwd_geom_go(dim3 grid, size_t smem, cudaStream_t st, const TxDev *tx, const TimeDev &tm,
+                               const GridDev &g, const float *x, double *Dg, int bpc, const int *base, int span)
+{
+    set_smem_attr((const void *)fwd_geom_kernel<METHOD, KIND>, smem);
+    fwd_geom_kernel<METHOD, KIND><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, bpc, base, span);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_geom(const TxDev *tx, int K, int kind, const TimeDev &tm, const GridDev &g, const float *x,
+                            double *Dg, int chunks, const int *base, int span, cudaStream_t st)
 {
     size_t smem = 2 * sizeof(float) * (size_t)span;
-    set_smem_attr((const void *)fwd_geom_kernel, smem);
     long long bpc = (g.nbricks + chunks - 1) / chunks;
     bpc = ((bpc + kWarpsPerBlock - 1) / kWarpsPerBlock) * kWarpsPerBlock;
     unsigned gx = (unsigned)((g.nbricks + bpc - 1) / bpc);
     cudaError_t e = cudaMemsetAsync(Dg, 0, sizeof(double) * (size_t)(tm.UL + 1) * K, st);
     if (e != cudaSuccess) return e;
-    fwd_geom_kernel<<<dim3(gx, (unsigned)K), kThreads, smem, st>>>(tx, tm, g, x, Dg, (int)bpc, base, span);
-    return cudaGetLastError();
+    const dim3 grid(gx, (unsigned)K);
+    const int b = (int)bpc;
+    if (tm.method == PAT_METHOD_POINT) {
+        if (kind == PAT_PLANE) return fwd_geom_go<PAT_METHOD_POINT, PAT_PLANE>(grid, smem, st, tx, tm, g, x, Dg, b, base, span);
+        if (kind == PAT_CYLINDER)
+            return fwd_geom_go<PAT_METHOD_POINT, PAT_CYLINDER>(grid, smem, st, tx, tm, g, x, Dg, b, base, span);
+        return fwd_geom_go<PAT_METHOD_POINT, kKindAny>(grid, smem, st, tx, tm, g, x, Dg, b, base, span);
+    }
+    if (kind == PAT_PLANE) return fwd_geom_go<PAT_METHOD_SURFACE, PAT_PLANE>(grid, smem, st, tx, tm, g, x, Dg, b, base, span);
+    if (kind == PAT_CYLINDER)
+        return fwd_geom_go<PAT_METHOD_SURFACE, PAT_CYLINDER>(grid, smem, st, tx, tm, g, x, Dg, b, base, span);
+    return fwd_geom_go<PAT_METHOD_SURFACE, kKindAny>(grid, smem, st, tx, tm, g, x, Dg, b, base, span);
 }
 
 cudaError_t launch_fwd_epilogue(const void *in, int in_stride, const float *W, int nW, int n_lo, const TimeDev &tm,
@@ -704,11 +726,21 @@ cudaError_t launch_adj_conv(const float *s, int from_v, const float *W, int nW, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_geom(const TxDev *tx, int K, const TimeDev &tm, const GridDev &g, const void *P, float *z,
-                            cudaStream_t st)
+cudaError_t launch_adj_geom(const TxDev *tx, int K, int kind, const TimeDev &tm, const GridDev &g, const void *P,
+                            float *z, cudaStream_t st)
 {
     unsigned grid = (unsigned)((g.nbricks + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    adj_geom_kernel<<<grid, kThreads, 0, st>>>(tx, K, tm, g, P, z);
+    if (tm.method == PAT_METHOD_POINT) {
+        if (kind == PAT_PLANE) adj_geom_kernel<PAT_METHOD_POINT, PAT_PLANE><<<grid, kThreads, 0, st>>>(tx, K, tm, g, P, z);
+        else if (kind == PAT_CYLINDER)
+            adj_geom_kernel<PAT_METHOD_POINT, PAT_CYLINDER><<<grid, kThreads, 0, st>>>(tx, K, tm, g, P, z);
+        else adj_geom_kernel<PAT_METHOD_POINT, kKindAny><<<grid, kThreads, 0, st>>>(tx, K, tm, g, P, z);
+    } else {
+        if (kind == PAT_PLANE) adj_geom_kernel<PAT_METHOD_SURFACE, PAT_PLANE><<<grid, kThreads, 0, st>>>(tx, K, tm, g, P, z);
+        else if (kind == PAT_CYLINDER)
+            adj_geom_kernel<PAT_METHOD_SURFACE, PAT_CYLINDER><<<grid, kThreads, 0, st>>>(tx, K, tm, g, P, z);
+        else adj_geom_kernel<PAT_METHOD_SURFACE, kKindAny><<<grid, kThreads, 0, st>>>(tx, K, tm, g, P, z);
+    }
     return cudaGetLastError();
 }
 
