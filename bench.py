@@ -70,12 +70,9 @@ def dist_env():
 
 def batches(args, rank, world, total_steps):
     """Angle batches for this rank: rank r takes batches r, r + world, ..."""
-    nb = max(1, N_ANGLES // args.batch_angles)
-    out = []
-    for i in range(total_steps):
-        b = (rank + i * world) % nb
-        out.append(np.arange(b * args.batch_angles, (b + 1) * args.batch_angles) * 2 * math.pi / N_ANGLES)
-    return out
+    from paper_2609_29253_gb300 import shard
+
+    return shard.angle_batches(N_ANGLES, args.batch_angles, rank, world, total_steps)
 
 
 class ClockSampler:
