@@ -48,7 +48,17 @@ enum { PAT_PLANE = 0, PAT_CYLINDER = 1 };
 enum { PAT_METHOD_SURFACE = 0, PAT_METHOD_POINT = 1 };
 enum { PAT_RBF_BUMP = 0, PAT_RBF_CONE = 1, PAT_RBF_WENDLAND = 2 };
 enum { PAT_EIR_GAUSS_SINE = 0, PAT_EIR_BOX = 1 };
-enum { PAT_FLAG_ALLOW_CLIP = 1 };
+/* Plan flags (pat_params.flags, OR-ed):
+ *   PAT_FLAG_ALLOW_CLIP  drop fine bins outside [0, U L) instead of failing
+ *                        plan creation;
+ *   PAT_FLAG_CONV_TC     run the temporal convolution (Eq. discrete_conv) and
+ *                        its transpose (App. G) as Toeplitz contractions on the
+ *                        tcgen05 tensor cores: BF16 operands split in two
+ *                        (hi + lo), hi*hi + hi*lo + lo*hi accumulated in FP32.
+ *                        Areas and accumulation of f stay FP32 / FP64; the
+ *                        convolution then carries about 16 significant bits
+ *                        per product instead of FP64 accumulation. */
+enum { PAT_FLAG_ALLOW_CLIP = 1, PAT_FLAG_CONV_TC = 2 };
 enum { PAT_OP_FORWARD = 1, PAT_OP_ADJOINT = 2, PAT_OP_RECON = 3 };
 
 /* Uniform voxel grid (Sec. 2.4): centres origin + pitch * (ix, iy, iz). */
@@ -116,6 +126,9 @@ typedef struct pat_plan_info {
     int64_t conv_clipped;     /* transducers whose filtered response leaves [0, U L) (dropped by definition) */
     double dist_min;          /* min over pairs of the distance to the element (Eq. min_dist) */
     int64_t fwd_blocks, adj_blocks;
+    int64_t tc_error;         /* PAT_FLAG_CONV_TC plans: non-zero if a tensor-core CTA gave up waiting on the
+                                 TMA engine or the tensor cores (its output tile is then left unwritten);
+                                 reading it synchronises with the plan's device */
 } pat_plan_info;
 
 /* Discrete system kernel (Eq. def_bh):
@@ -138,7 +151,8 @@ pat_status pat_system_kernel(const pat_system *sys, double c, double fs, int32_t
  * q1/q2 < 1 for the point method, frame not orthonormal, theta_max not in
  * (0, pi/2)); PAT_ERR_GEOMETRY (separation, Ass. 1(iii) and Prop. 3);
  * PAT_ERR_WINDOW (bins outside [0, U L) without PAT_FLAG_ALLOW_CLIP);
- * PAT_ERR_UNSUPPORTED (U L too large for the shared-memory histogram);
+ * PAT_ERR_UNSUPPORTED (U L too large for the shared-memory histogram, or a
+ * tap window too wide for the tensor-core convolution's shared memory);
  * PAT_ERR_CUDA.  *out is NULL on failure. */
 pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, const pat_transducer *tx, int32_t K,
                            const pat_params *params, double kappa, const double *taps_host, int32_t n_taps,

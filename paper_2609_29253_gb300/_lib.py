@@ -19,6 +19,7 @@ PAT_OK = 0
 PAT_ERR_WORKSPACE = 4
 PAT_OP_FORWARD, PAT_OP_ADJOINT, PAT_OP_RECON = 1, 2, 3
 PAT_FLAG_ALLOW_CLIP = 1
+PAT_FLAG_CONV_TC = 2
 _STATUS = {0: "PAT_OK", 1: "PAT_ERR_INVALID_ARG", 2: "PAT_ERR_GEOMETRY", 3: "PAT_ERR_WINDOW",
            4: "PAT_ERR_WORKSPACE", 5: "PAT_ERR_CUDA", 6: "PAT_ERR_UNSUPPORTED"}
 
@@ -47,7 +48,8 @@ class pat_plan_info(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("N", "K", "L", "U", "UL", "dl", "method", "n_taps", "n_lo", "bin_lo",
                                          "bin_hi", "area_evals", "pair_bins", "quad_evals", "clipped_pairs",
                                          "conv_clipped")] + \
-               [("dist_min", C.c_double), ("fwd_blocks", C.c_int64), ("adj_blocks", C.c_int64)]
+               [("dist_min", C.c_double), ("fwd_blocks", C.c_int64), ("adj_blocks", C.c_int64),
+                ("tc_error", C.c_int64)]
 
 
 EXPORTS = ["pat_system_kernel", "pat_plan_create", "pat_plan_destroy", "pat_plan_get_info", "pat_workspace_bytes",

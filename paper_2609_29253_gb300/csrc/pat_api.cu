@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "pat.h"
+#include "pat_conv_tc.cuh"
 #include "pat_kernels.cuh"
 
 using namespace pat;
@@ -33,6 +34,11 @@ struct pat_plan {
     int smem_optin;
     int kind_all;   // PAT_PLANE / PAT_CYLINDER if every element has it, else kKindAny
     double *scal; // device scalars for pat_recon
+    // PAT_FLAG_CONV_TC: tensor-core convolution tables and error word
+    bool tc;
+    TcGeometry tcg;
+    uint8_t *tc_fwd_tab, *tc_adj_tab;
+    int *tc_err;
     pat_plan_info info;
 };
 
@@ -101,6 +107,8 @@ static pat_status validate(const pat_grid *grid, const pat_transducer *tx, int K
         return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: point method needs q1, q2 >= 1");
     if (!(kappa > 0)) return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: kappa must be > 0");
     if (n_taps < 1) return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: n_taps must be >= 1");
+    if (p->flags & ~(PAT_FLAG_ALLOW_CLIP | PAT_FLAG_CONV_TC))
+        return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: unknown flags 0x%x", p->flags);
     for (int k = 0; k < K; ++k) {
         const pat_transducer &t = tx[k];
         int kind = (int)t.kind;
@@ -177,6 +185,15 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
     p->n_lo = n_lo;
     p->nW = n_taps + params->U - 1;
     p->smem_optin = optin;
+    p->tc = (params->flags & PAT_FLAG_CONV_TC) != 0;
+    if (p->tc) {
+        p->tcg = tc_geometry(n_taps, params->U, params->L, n_lo);
+        if (p->tcg.fwd_smem > (size_t)optin || p->tcg.adj_smem > (size_t)optin) {
+            delete p;
+            return fail(PAT_ERR_UNSUPPORTED, "tensor-core convolution needs %zu bytes of shared memory per block, "
+                        "device has %d", std::max(p->tcg.fwd_smem, p->tcg.adj_smem), optin);
+        }
+    }
     size_t need_epi = sizeof(float) * (size_t)(tm.UL + p->nW) + 64;
     size_t need_adj = sizeof(float) * (size_t)(tm.L + p->nW + tm.UL) + 64;
     if (need_epi > (size_t)optin || need_adj > (size_t)optin) {
@@ -214,6 +231,19 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
             launch_combine_taps(p->taps, n_taps, params->U, p->W, s) != cudaSuccess) {
             rc = fail(PAT_ERR_CUDA, "pat_plan_create: setup kernels failed");
             break;
+        }
+        if (p->tc) {
+            if (cudaMalloc(&p->tc_fwd_tab, p->tcg.fwd_table_bytes) != cudaSuccess ||
+                cudaMalloc(&p->tc_adj_tab, p->tcg.adj_table_bytes) != cudaSuccess ||
+                cudaMalloc(&p->tc_err, sizeof(int)) != cudaSuccess) {
+                rc = fail(PAT_ERR_CUDA, "pat_plan_create: cudaMalloc failed");
+                break;
+            }
+            if (cudaMemsetAsync(p->tc_err, 0, sizeof(int), s) != cudaSuccess ||
+                launch_tc_tables(p->taps, n_taps, params->U, p->tcg, p->tc_fwd_tab, p->tc_adj_tab, s) != cudaSuccess) {
+                rc = fail(PAT_ERR_CUDA, "pat_plan_create: tensor-core tables failed");
+                break;
+            }
         }
         // scan every pair once
         void *sbuf = nullptr;
@@ -336,6 +366,9 @@ extern "C" pat_status pat_plan_destroy(pat_plan *p)
     cudaFree(p->W);
     cudaFree(p->fwd_base);
     cudaFree(p->scal);
+    cudaFree(p->tc_fwd_tab);
+    cudaFree(p->tc_adj_tab);
+    cudaFree(p->tc_err);
     cudaSetDevice(cur);
     delete p;
     return PAT_OK;
@@ -345,11 +378,27 @@ extern "C" pat_status pat_plan_get_info(const pat_plan *p, pat_plan_info *info)
 {
     if (!p || !info) return fail(PAT_ERR_INVALID_ARG, "pat_plan_get_info: null pointer");
     *info = p->info;
+    info->tc_error = 0;
+    if (p->tc) {
+        int e = 0, cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(p->device);
+        cudaError_t ce = cudaMemcpy(&e, p->tc_err, sizeof(int), cudaMemcpyDeviceToHost);
+        cudaSetDevice(cur);
+        if (ce != cudaSuccess) return fail(PAT_ERR_CUDA, "pat_plan_get_info: %s", cudaGetErrorString(ce));
+        info->tc_error = e;
+    }
     return PAT_OK;
 }
 
-static size_t ws_fwd(const pat_plan *p) { return align256(sizeof(double) * (size_t)(p->tm.UL + 1) * p->K); }
-static size_t ws_adj(const pat_plan *p) { return align256(sizeof(float2) * (size_t)(p->tm.UL + 1) * p->K); }
+// forward: difference array D [K][UL + 1] doubles, then (tensor-core
+// convolution) f [K][UL] floats; adjoint: prefix sums P [K][UL + 1] float2,
+// then (tensor-core convolution) v [K][UL] floats
+static size_t ws_D(const pat_plan *p) { return align256(sizeof(double) * (size_t)(p->tm.UL + 1) * p->K); }
+static size_t ws_P(const pat_plan *p) { return align256(sizeof(float2) * (size_t)(p->tm.UL + 1) * p->K); }
+static size_t ws_f(const pat_plan *p) { return p->tc ? align256(sizeof(float) * (size_t)p->tm.UL * p->K) : 0; }
+static size_t ws_fwd(const pat_plan *p) { return ws_D(p) + ws_f(p); }
+static size_t ws_adj(const pat_plan *p) { return ws_P(p) + ws_f(p); }
 static size_t ws_recon(const pat_plan *p)
 {
     return std::max(ws_fwd(p), ws_adj(p)) + align256(sizeof(float) * (size_t)p->K * p->tm.L) +
@@ -374,18 +423,34 @@ static pat_status check_ws(const pat_plan *p, void *ws, size_t bytes, size_t nee
     return PAT_OK;
 }
 
+// s = A x (s may be null: geometric stage only, into f).  With the
+// tensor-core convolution the epilogue writes f into the workspace and the
+// tcgen05 kernel filters and downsamples it.
 static pat_status enqueue_forward(pat_plan *p, const float *x, float *s, float *f, void *ws, cudaStream_t st)
 {
     double *D = (double *)ws;
     CK(launch_fwd_geom(p->tx, p->K, p->kind_all, p->tm, p->g, x, D, p->fwd_chunks, p->fwd_base, p->fwd_span, st));
     int mode = p->tm.method == PAT_METHOD_POINT ? 1 : 0;
+    if (p->tc && s) {
+        float *fw = (float *)((char *)ws + ws_D(p));
+        CK(launch_fwd_epilogue(D, p->tm.UL + 1, p->W, p->nW, p->n_lo, p->tm, mode, p->K, nullptr, fw, st));
+        CK(launch_conv_tc_fwd(fw, p->tc_fwd_tab, p->tcg, p->K, p->tm.L, p->tm.U, s, p->tc_err, st));
+        return PAT_OK;
+    }
     CK(launch_fwd_epilogue(D, p->tm.UL + 1, p->W, p->nW, p->n_lo, p->tm, mode, p->K, s, f, st));
     return PAT_OK;
 }
 
+// z = A^T s (from_v = 0) or the geometric transpose of v (from_v = 1).
 static pat_status enqueue_adjoint(pat_plan *p, const float *in, int from_v, float *z, void *ws, cudaStream_t st)
 {
     int mode = p->tm.method == PAT_METHOD_POINT ? 1 : 0;
+    if (p->tc && !from_v) {
+        float *vw = (float *)((char *)ws + ws_P(p));
+        CK(launch_conv_tc_adj(in, p->tc_adj_tab, p->tcg, p->K, p->tm.L, p->tm.U, vw, p->tc_err, st));
+        in = vw;
+        from_v = 1;
+    }
     CK(launch_adj_conv(in, from_v, p->W, p->nW, p->n_lo, p->tm, mode, p->K, ws, st));
     CK(launch_adj_geom(p->tx, p->K, p->kind_all, p->tm, p->g, ws, z, st));
     return PAT_OK;
@@ -414,6 +479,10 @@ extern "C" pat_status pat_conv_forward(pat_plan *p, const float *f, float *s, vo
 {
     g_err.clear();
     if (!p || !f || !s) return fail(PAT_ERR_INVALID_ARG, "pat_conv_forward: null pointer");
+    if (p->tc) {
+        CK(launch_conv_tc_fwd(f, p->tc_fwd_tab, p->tcg, p->K, p->tm.L, p->tm.U, s, p->tc_err, (cudaStream_t)stream));
+        return PAT_OK;
+    }
     CK(launch_fwd_epilogue(f, p->tm.UL, p->W, p->nW, p->n_lo, p->tm, 2, p->K, s, nullptr, (cudaStream_t)stream));
     return PAT_OK;
 }
@@ -422,6 +491,10 @@ extern "C" pat_status pat_conv_adjoint(pat_plan *p, const float *s, float *v, vo
 {
     g_err.clear();
     if (!p || !s || !v) return fail(PAT_ERR_INVALID_ARG, "pat_conv_adjoint: null pointer");
+    if (p->tc) {
+        CK(launch_conv_tc_adj(s, p->tc_adj_tab, p->tcg, p->K, p->tm.L, p->tm.U, v, p->tc_err, (cudaStream_t)stream));
+        return PAT_OK;
+    }
     CK(launch_adj_conv(s, 0, p->W, p->nW, p->n_lo, p->tm, 2, p->K, v, (cudaStream_t)stream));
     return PAT_OK;
 }

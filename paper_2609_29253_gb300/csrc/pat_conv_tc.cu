@@ -1,0 +1,553 @@
+// pat_conv_tc.cu -- the temporal convolution of A and its transpose as
+// Toeplitz contractions on the tcgen05 tensor cores (sm_103a).
+//
+// Forward (Eq. discrete_conv, filter then downsample by U):
+//   s[k][l] = sum_j W[j] f[k][U l + c - j],   c = U - 1 - n_lo,
+// with W = box_U * h-bar / U (nW = T + U - 1 taps) and f = 0 outside
+// [0, U L).  For an output tile l = l0 + i, i < 128, the inputs lie in the
+// window m = m0 + mu, m0 = U l0 + c - (nW - 1), mu < 127 U + nW, and
+//   s[k][l0 + i] = sum_mu Tf[i][mu] f[k][m0 + mu],  Tf[i][mu] = W[U i + nW - 1 - mu],
+// where Tf does not depend on l0: one constant Toeplitz matrix for every tile.
+//
+// Adjoint (App. G, transpose of the above):
+//   v[k][b] = sum_l s[k][l] W[U l + c - b].
+// Split b = U m + p (polyphase, p < U) and l = m + d:
+//   v[k][U (m0 + i) + p] = sum_lambda Ta_p[i][lambda] s[k][m0 + d0 + lambda],
+//   Ta_p[i][lambda] = W[U (d0 + lambda - i) + c - p],
+// with d0 the smallest d that any phase reaches; again one constant matrix per
+// phase for every tile m0.
+//
+// Each CTA computes one D = T (128 x Kw) x B^T (Kw x 64) tile: M = 128 output
+// samples, N = 64 transducers, in K stages of 64.  Operands are BF16 split in
+// two (x = hi + lo, hi = bf16(x), lo = bf16(x - hi)) and the tile is
+// accumulated as hi*hi + hi*lo + lo*hi in FP32 in tensor memory, which keeps
+// about 16 significant bits per product (a single BF16 pass loses too much to
+// the cancellation of the band-pass kernel: Sum h-bar = 0).
+//
+//   * T (hi and lo) is precomputed once per plan, per stage, in the exact
+//     shared-memory operand layout, and brought in by one bulk copy (TMA,
+//     cp.async.bulk) per stage, completing on an mbarrier;
+//   * B (f or s rows, FP32 in HBM) is read with coalesced loads, split, and
+//     stored in the operand layout by all threads;
+//   * one thread issues tcgen05.mma (kind::f16, BF16 in, FP32 accumulate,
+//     M = 128, N = 64, K = 16) and tcgen05.commit onto an mbarrier that frees
+//     the stage's buffers; two buffers alternate;
+//   * the accumulator (128 lanes x 64 columns of TMEM) is read back with
+//     tcgen05.ld, each warp its 32 lanes, and stored to s or v.
+// Operand layout (no swizzle, K-major): 8 x 8 core matrices of 16-bit values
+// (8 rows x 16 bytes, 128 contiguous bytes); core matrix (row group g, K
+// group q) at q * LBO + g * 128.  Every wait is bounded: after about two seconds
+// the CTA records an error code, finishes what it issued and returns.
+#include <cuda_bf16.h>
+
+#include "pat_conv_tc.cuh"
+
+namespace pat {
+
+namespace {
+
+constexpr int kM = kTcM, kN = kTcN, kKS = kTcKStage;
+constexpr int kAHalf = kM * kKS * 2;           // bytes of one T stage (hi or lo)
+constexpr int kBHalf = kN * kKS * 2;           // bytes of one B stage (hi or lo)
+constexpr uint32_t kLboA = kM * 16, kLboB = kN * 16, kSbo = 128;
+constexpr long long kSpinCycles = 4000000000LL; // about 2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor of tcgen05 (no swizzle): start address,
+// leading-dimension byte offset (K direction), stride byte offset (M / N
+// direction), descriptor version 1 at bits 46-47.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9 and 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at
+// bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
+                            ((uint32_t)(kM >> 4) << 24);
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}\n"
+                 : "=r"(ok)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase of `bar` with the given parity to complete; false after
+// about two seconds.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity)) {
+        __nanosleep(64);
+        if (clock64() - t0 > kSpinCycles) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// One bulk copy global -> shared through the TMA engine, completing on bar.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate)
+{
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "setp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+                 "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&r)[16])
+{
+    uint32_t u[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                 : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+                   "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]),
+                   "=r"(u[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) r[j] = __uint_as_float(u[j]);
+}
+
+// byte offset of element (row, kk) in a no-swizzle K-major operand tile with
+// `rows` rows and kKS columns
+__device__ __forceinline__ uint32_t op_off(int row, int kk, int rows)
+{
+    return (uint32_t)((kk >> 3) * (rows * 16) + (row >> 3) * 128 + (row & 7) * 16 + (kk & 7) * 2);
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b)
+{
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// B stage: rows n < kN (transducers k0 + n of src, row length len, row
+// stride ld), columns kk < kKS (source index start + kk); zero outside the
+// row and beyond K.  One 16-byte core-matrix row (8 values) per item.
+__device__ __forceinline__ void build_b(const float *__restrict__ src, long long ld, int len, int K, int k0, int start,
+                                        uint8_t *bhi, uint8_t *blo)
+{
+    for (int item = threadIdx.x; item < kN * (kKS / 8); item += blockDim.x) {
+        const int n = item / (kKS / 8), q = item % (kKS / 8);
+        const int k = k0 + n;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int m = start + q * 8 + e;
+            v[e] = (k < K && m >= 0 && m < len) ? __ldg(&src[(long long)k * ld + m]) : 0.f;
+        }
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * e]), h1 = __float2bfloat16_rn(v[2 * e + 1]);
+            const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * e] - __bfloat162float(h0));
+            const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * e + 1] - __bfloat162float(h1));
+            h[e] = pack2(h0, h1);
+            l[e] = pack2(l0, l1);
+        }
+        const uint32_t off = op_off(n, q * 8, kN);
+        *reinterpret_cast<uint4 *>(bhi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4 *>(blo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+}
+
+// Shared memory of one CTA: two A buffers (T hi + lo per stage), B buffers,
+// mbarriers and the TMEM address slot.
+struct TcSmem {
+    uint8_t *a[2];  // kAHalf hi then kAHalf lo
+    uint8_t *b;     // nb buffers of 2 kBHalf (hi, lo)
+    uint32_t full[2], empty[2];
+    uint32_t *tslot;
+    int *abort_flag;
+};
+
+__device__ __forceinline__ TcSmem carve(uint8_t *base, int nb)
+{
+    TcSmem s;
+    s.a[0] = base;
+    s.a[1] = base + 2 * kAHalf;
+    s.b = base + 4 * kAHalf;
+    uint8_t *tail = s.b + (size_t)nb * 2 * kBHalf;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(tail);
+    s.full[0] = smem_u32(&bars[0]);
+    s.full[1] = smem_u32(&bars[1]);
+    s.empty[0] = smem_u32(&bars[2]);
+    s.empty[1] = smem_u32(&bars[3]);
+    s.tslot = reinterpret_cast<uint32_t *>(&bars[4]);
+    s.abort_flag = reinterpret_cast<int *>(&bars[5]);
+    return s;
+}
+
+// barrier set-up and TMEM allocation (warp 0), kN FP32 columns
+__device__ __forceinline__ uint32_t tc_setup(const TcSmem &S)
+{
+    if (threadIdx.x == 0) {
+        mbar_init(S.full[0], 1);
+        mbar_init(S.full[1], 1);
+        mbar_init(S.empty[0], 1);
+        mbar_init(S.empty[1], 1);
+        *S.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(S.tslot)),
+                     "r"((uint32_t)kN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    return *S.tslot;
+}
+
+__device__ __forceinline__ void tc_teardown(uint32_t tmem)
+{
+    fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kN)
+                     : "memory");
+}
+
+// Issues the 3 split products of one stage: K = kKS in kKS / 16 MMAs each.
+__device__ __forceinline__ void issue_stage(uint32_t tmem, const uint8_t *a, const uint8_t *bhi, const uint8_t *blo,
+                                            bool first)
+{
+    const uint32_t ahi = smem_u32(a), alo = smem_u32(a + kAHalf), bh = smem_u32(bhi), bl = smem_u32(blo);
+#pragma unroll
+    for (int ks = 0; ks < kKS / 16; ++ks) {
+        const uint32_t oa = ks * 2 * kLboA, ob = ks * 2 * kLboB;
+        mma_bf16(tmem, sdesc(ahi + oa, kLboA, kSbo), sdesc(bh + ob, kLboB, kSbo), (first && ks == 0) ? 0u : 1u);
+        mma_bf16(tmem, sdesc(ahi + oa, kLboA, kSbo), sdesc(bl + ob, kLboB, kSbo), 1u);
+        mma_bf16(tmem, sdesc(alo + oa, kLboA, kSbo), sdesc(bh + ob, kLboB, kSbo), 1u);
+    }
+}
+
+// Records a failed wait: the CTA stops issuing, drains and returns.
+__device__ __forceinline__ void note_timeout(const TcSmem &S, int *err, int code)
+{
+    *S.abort_flag = 1;
+    atomicExch(err, code);
+}
+
+// Issue state of the one thread that drives the TMA engine and the tensor
+// cores (thread 0).  Stage q uses buffer q & 1; its copy completes phase
+// q >> 1 of full[q & 1] and its MMAs (through tcgen05.commit) phase q >> 1 of
+// empty[q & 1].
+struct Pipe {
+    int issued = 0, landed = 0, committed = 0;
+
+    // T stage q into buffer q & 1, once the MMAs of stage q - 2 (the last
+    // readers of that buffer) are done.
+    __device__ __forceinline__ bool load(const TcSmem &S, const uint8_t *tab, int q)
+    {
+        const int b = q & 1;
+        if (q >= 2 && !mbar_wait(S.empty[b], ((q - 2) >> 1) & 1)) return false;
+        mbar_expect_tx(S.full[b], 2 * kAHalf);
+        bulk_g2s(smem_u32(S.a[b]), tab + (size_t)q * 2 * kAHalf, 2 * kAHalf, S.full[b]);
+        issued = q + 1;
+        return true;
+    }
+    __device__ __forceinline__ bool mma(const TcSmem &S, uint32_t tmem, int q, const uint8_t *bhi, bool first)
+    {
+        const int b = q & 1;
+        if (!mbar_wait(S.full[b], (q >> 1) & 1)) return false;
+        landed = q + 1;
+        fence_after();
+        issue_stage(tmem, S.a[b], bhi, bhi + kBHalf, first);
+        mma_commit(S.empty[b]);
+        committed = q + 1;
+        return true;
+    }
+    // after a timeout: bounded waits for every copy and MMA still in flight
+    __device__ __forceinline__ void drain(const TcSmem &S) const
+    {
+        for (int q = landed; q < issued; ++q) mbar_wait(S.full[q & 1], (q >> 1) & 1);
+        if (committed > 0) mbar_wait(S.empty[(committed - 1) & 1], ((committed - 1) >> 1) & 1);
+    }
+};
+
+} // namespace
+
+// ---------------------------------------------------------------------------
+// Forward: grid (ceil(L / 128), ceil(K / 64)); Tf: nst stages of 2 kAHalf.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTcThreads) conv_tc_fwd_kernel(const float *__restrict__ f, const uint8_t *__restrict__ Tf,
+                                                                 int nst, int m0off, int K, int L, int UL, int U,
+                                                                 float *__restrict__ s, int *__restrict__ err)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const TcSmem S = carve(smem_raw, 2);
+    const uint32_t tmem = tc_setup(S);
+    const int l0 = blockIdx.x * kM, k0 = blockIdx.y * kN;
+    const long long m0 = (long long)U * l0 + m0off;
+    Pipe pipe;
+    if (threadIdx.x == 0 && !pipe.load(S, Tf, 0)) note_timeout(S, err, 1);
+    for (int st = 0; st < nst; ++st) {
+        const int b = st & 1;
+        uint8_t *bhi = S.b + (size_t)b * 2 * kBHalf;
+        // the B buffer was last read by the MMAs of stage st - 2
+        if (st >= 2 && !*S.abort_flag && !mbar_wait(S.empty[b], ((st - 2) >> 1) & 1)) note_timeout(S, err, 2);
+        __syncthreads();
+        if (*S.abort_flag) break;
+        build_b(f, UL, UL, K, k0, (int)(m0 + (long long)st * kKS), bhi, bhi + kBHalf);
+        fence_proxy_async();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            if (st + 1 < nst && !pipe.load(S, Tf, st + 1)) note_timeout(S, err, 3);
+            else if (!pipe.mma(S, tmem, st, bhi, st == 0)) note_timeout(S, err, 4);
+        }
+    }
+    __syncthreads();
+    bool ok = !*S.abort_flag;
+    // the last commit covers every earlier MMA of this thread
+    if (ok && !mbar_wait(S.empty[(nst - 1) & 1], ((nst - 1) >> 1) & 1)) {
+        atomicExch(err, 5);
+        ok = false;
+    }
+    fence_after();
+    if (ok) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int l = l0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c = 0; c < kN; c += 16) {
+            float r[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
+            if (l < L) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int k = k0 + c + j;
+                    if (k < K) s[(long long)k * L + l] = r[j];
+                }
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        pipe.drain(S);
+    }
+    tc_teardown(tmem);
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint: grid (ceil(L / 128), ceil(K / 64)); Ta: U phases x nst stages of
+// 2 kAHalf.  B (the s window, nst stages) is built once and reused by every
+// phase; T stages stream through two buffers.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTcThreads) conv_tc_adj_kernel(const float *__restrict__ s, const uint8_t *__restrict__ Ta,
+                                                                 int nst, int d0, int K, int L, int UL, int U,
+                                                                 float *__restrict__ v, int *__restrict__ err)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    const TcSmem S = carve(smem_raw, nst);
+    const uint32_t tmem = tc_setup(S);
+    const int m0 = blockIdx.x * kM, k0 = blockIdx.y * kN;
+    Pipe pipe;
+    if (threadIdx.x == 0 && !pipe.load(S, Ta, 0)) note_timeout(S, err, 1);
+    for (int st = 0; st < nst; ++st) {
+        uint8_t *bhi = S.b + (size_t)st * 2 * kBHalf;
+        build_b(s, L, L, K, k0, m0 + d0 + st * kKS, bhi, bhi + kBHalf);
+    }
+    fence_proxy_async();
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m = m0 + warp * 32 + lane;
+    const int total = U * nst; // (phase, stage) pairs in order
+    bool ok = true;
+    for (int g = 0; g < total; ++g) {
+        const int p = g / nst, st = g % nst;
+        if (threadIdx.x == 0 && !*S.abort_flag) {
+            if (g + 1 < total && !pipe.load(S, Ta, g + 1)) note_timeout(S, err, 3);
+            else if (!pipe.mma(S, tmem, g, S.b + (size_t)st * 2 * kBHalf, st == 0)) note_timeout(S, err, 4);
+        }
+        if (st != nst - 1) continue;
+        // phase p is complete once its last commit lands: read it out
+        __syncthreads();
+        if (*S.abort_flag) {
+            ok = false;
+            break;
+        }
+        if (!mbar_wait(S.empty[g & 1], (g >> 1) & 1)) {
+            atomicExch(err, 5);
+            *S.abort_flag = 1;
+        }
+        __syncthreads();
+        if (*S.abort_flag) {
+            ok = false;
+            break;
+        }
+        fence_after();
+#pragma unroll 1
+        for (int c = 0; c < kN; c += 16) {
+            float r[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
+            if (m < L) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int k = k0 + c + j;
+                    if (k < K) v[(long long)k * UL + (long long)U * m + p] = r[j];
+                }
+            }
+        }
+        // every lane's reads of this phase finish before the next phase's
+        // first MMA overwrites the accumulator
+        fence_before();
+        __syncthreads();
+        fence_after();
+    }
+    if (!ok && threadIdx.x == 0) pipe.drain(S);
+    tc_teardown(tmem);
+}
+
+// ---------------------------------------------------------------------------
+// Operand tables (plan set-up, FP64 taps -> BF16 hi / lo in the operand layout)
+// ---------------------------------------------------------------------------
+// W[j] = (1/U) sum_{u<U} h-bar[j - (U-1) + u] in FP64
+__device__ double w64(const double *__restrict__ taps, int T, int U, int j)
+{
+    if (j < 0 || j >= T + U - 1) return 0.0;
+    double acc = 0.0;
+    for (int u = 0; u < U; ++u) {
+        const int t = j - (U - 1) + u;
+        if (t >= 0 && t < T) acc += taps[t];
+    }
+    return acc / U;
+}
+
+__device__ __forceinline__ void put_split(uint8_t *stage, int row, int kk, double w)
+{
+    const __nv_bfloat16 hi = __float2bfloat16_rn((float)w);
+    const __nv_bfloat16 lo = __float2bfloat16_rn((float)(w - (double)__bfloat162float(hi)));
+    const uint32_t off = op_off(row, kk, kM);
+    *reinterpret_cast<__nv_bfloat16 *>(stage + off) = hi;
+    *reinterpret_cast<__nv_bfloat16 *>(stage + kAHalf + off) = lo;
+}
+
+// Tf[st]: element (i, kk) = W[U i + nW - 1 - (st kKS + kk)]
+__global__ void tc_table_fwd_kernel(const double *__restrict__ taps, int T, int U, int nst, uint8_t *__restrict__ Tf)
+{
+    const long long n = (long long)nst * kM * kKS;
+    const int nW = T + U - 1;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int st = (int)(e / (kM * kKS)), r = (int)(e % (kM * kKS)), i = r / kKS, kk = r % kKS;
+        const int mu = st * kKS + kk;
+        put_split(Tf + (size_t)st * 2 * kAHalf, i, kk, w64(taps, T, U, U * i + nW - 1 - mu));
+    }
+}
+
+// Ta[p][st]: element (i, kk) = W[U (d0 + lambda - i) + c - p], lambda = st kKS + kk
+__global__ void tc_table_adj_kernel(const double *__restrict__ taps, int T, int U, int nst, int d0, int c,
+                                    uint8_t *__restrict__ Ta)
+{
+    const long long n = (long long)U * nst * kM * kKS;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const long long g = e / (kM * kKS);
+        const int r = (int)(e % (kM * kKS)), i = r / kKS, kk = r % kKS;
+        const int p = (int)(g / nst), st = (int)(g % nst);
+        const int lam = st * kKS + kk;
+        put_split(Ta + (size_t)g * 2 * kAHalf, i, kk, w64(taps, T, U, U * (d0 + lam - i) + c - p));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+TcGeometry tc_geometry(int T, int U, int L, int n_lo)
+{
+    TcGeometry g;
+    const int nW = T + U - 1, c = U - 1 - n_lo;
+    g.m0off = c - (nW - 1);
+    const int kw = (kM - 1) * U + nW; // forward window length
+    g.nst_fwd = (kw + kKS - 1) / kKS;
+    // adjoint: d over all phases with 0 <= U d + c - p < nW
+    int dmin = 1 << 30, dmax = -(1 << 30);
+    for (int p = 0; p < U; ++p)
+        for (int j = 0; j < nW; ++j)
+            if ((j - c + p) % U == 0) { // U d = j - c + p
+                const int d = (j - c + p) / U;
+                dmin = d < dmin ? d : dmin;
+                dmax = d > dmax ? d : dmax;
+            }
+    g.d0 = dmin;
+    const int ka = dmax - dmin + kM;
+    g.nst_adj = (ka + kKS - 1) / kKS;
+    g.c = c;
+    g.fwd_table_bytes = (size_t)g.nst_fwd * 2 * kAHalf;
+    g.adj_table_bytes = (size_t)U * g.nst_adj * 2 * kAHalf;
+    g.fwd_smem = 4 * kAHalf + 2 * 2 * kBHalf + 64;
+    g.adj_smem = 4 * kAHalf + (size_t)g.nst_adj * 2 * kBHalf + 64;
+    (void)L;
+    return g;
+}
+
+cudaError_t launch_tc_tables(const double *taps, int T, int U, const TcGeometry &g, uint8_t *Tf, uint8_t *Ta,
+                             cudaStream_t st)
+{
+    tc_table_fwd_kernel<<<304, 256, 0, st>>>(taps, T, U, g.nst_fwd, Tf);
+    tc_table_adj_kernel<<<608, 256, 0, st>>>(taps, T, U, g.nst_adj, g.d0, g.c, Ta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_conv_tc_fwd(const float *f, const uint8_t *Tf, const TcGeometry &g, int K, int L, int U, float *s,
+                               int *err, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute((const void *)conv_tc_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)g.fwd_smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((L + kM - 1) / kM), (unsigned)((K + kN - 1) / kN));
+    conv_tc_fwd_kernel<<<grid, kTcThreads, g.fwd_smem, st>>>(f, Tf, g.nst_fwd, g.m0off, K, L, U * L, U, s, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_conv_tc_adj(const float *s, const uint8_t *Ta, const TcGeometry &g, int K, int L, int U, float *v,
+                               int *err, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute((const void *)conv_tc_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)g.adj_smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((L + kM - 1) / kM), (unsigned)((K + kN - 1) / kN));
+    conv_tc_adj_kernel<<<grid, kTcThreads, g.adj_smem, st>>>(s, Ta, g.nst_adj, g.d0, K, L, U * L, U, v, err);
+    return cudaGetLastError();
+}
+
+} // namespace pat

@@ -1,0 +1,38 @@
+// pat_conv_tc.cuh -- host side of the tensor-core (tcgen05) temporal
+// convolution and its transpose (pat_conv_tc.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace pat {
+
+constexpr int kTcM = 128;      // output samples per tile (MMA M)
+constexpr int kTcN = 64;       // transducers per tile (MMA N)
+constexpr int kTcKStage = 64;  // contraction length per pipeline stage
+constexpr int kTcThreads = 128;
+
+// Tile geometry of one plan (taps, U, n_lo fixed).
+struct TcGeometry {
+    int c;         // U - 1 - n_lo
+    int m0off;     // forward window start: m0 = U l0 + m0off
+    int nst_fwd;   // forward stages per tile
+    int d0;        // adjoint window start: l = m0 + d0 + lambda
+    int nst_adj;   // adjoint stages per tile and phase
+    size_t fwd_table_bytes, adj_table_bytes;
+    size_t fwd_smem, adj_smem; // dynamic shared memory per CTA
+};
+
+TcGeometry tc_geometry(int T, int U, int L, int n_lo);
+// Toeplitz operand tables (BF16 hi / lo, shared-memory layout) from the FP64 taps.
+cudaError_t launch_tc_tables(const double *taps, int T, int U, const TcGeometry &g, uint8_t *Tf, uint8_t *Ta,
+                             cudaStream_t st);
+// s[K][L] from f[K][U L]; v[K][U L] from s[K][L].  err: device int, set
+// non-zero if a CTA gave up waiting on the TMA engine or the tensor cores.
+cudaError_t launch_conv_tc_fwd(const float *f, const uint8_t *Tf, const TcGeometry &g, int K, int L, int U, float *s,
+                               int *err, cudaStream_t st);
+cudaError_t launch_conv_tc_adj(const float *s, const uint8_t *Ta, const TcGeometry &g, int K, int L, int U, float *v,
+                               int *err, cudaStream_t st);
+
+} // namespace pat

@@ -1,0 +1,110 @@
+"""GPU parity of the tensor-core (tcgen05) temporal convolution, plans created
+with PAT_FLAG_CONV_TC, against the FP64 oracle, through the C ABI.
+
+The convolution runs with BF16 operands split in two (x = hi + lo) and the
+products hi*hi + hi*lo + lo*hi accumulated in FP32, so each product keeps
+about 16 significant bits.  Bound: rel L2 <= 1e-4 on every stage and on the
+whole A and A^T (the target for the reduced-precision convolution is 1e-3; a
+single BF16 pass gives about 1e-2 on these kernels because Sum h-bar = 0
+makes the outputs small against the terms).  Sizes span several 128-sample
+output tiles, a ragged last tile, a ragged transducer tile (K not a multiple
+of 64) and more than one transducer tile.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2609_29253_gb300 import workloads as W  # noqa: E402
+
+TC_TOL = 1e-4
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_29253_gb300 import api as A
+
+    return A
+
+
+def _stages(api, orc, w, seed):
+    taps = orc.taps_for(w)
+    plan = api.Plan(w, taps=taps, conv_tc=True, allow_clip=True)  # the stages alone: any time window
+    rng = np.random.default_rng(seed)
+    f = rng.standard_normal((w.K, w.UL)).astype(np.float32)
+    s = plan.conv_forward(torch.from_numpy(f).cuda()).cpu().numpy()
+    s_ref = orc.conv_forward(w, taps, f.astype(np.float64))
+    y = rng.standard_normal((w.K, w.L)).astype(np.float32)
+    v = plan.conv_adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
+    v_ref = orc.conv_adjoint(w, taps, y.astype(np.float64))
+    assert plan.info["tc_error"] == 0 and api._lib.pat_plan_get_info(plan.handle)["tc_error"] == 0
+    return rel(s, s_ref), rel(v, v_ref)
+
+
+@pytest.mark.parametrize("L,n_angles,n_el", [(1024, 2, 3), (300, 10, 8), (129, 3, 43)])
+def test_conv_stages_tensor_cores(api, oracle_mod, L, n_angles, n_el):
+    """f -> s and s -> v alone: L = 1024 (8 tiles), 300 (ragged), 129 (one
+    sample in the last tile); K = 6, 80 (two transducer tiles), 129."""
+    w = W.small_cylinder(n_vox=4, n_angles=n_angles, n_el=n_el, L=L)
+    es, ev = _stages(api, oracle_mod, w, seed=L)
+    assert es <= TC_TOL, es
+    assert ev <= TC_TOL, ev
+
+
+def test_conv_stages_planar_taps(api, oracle_mod):
+    """The planar c1 system's kernel (another tap window)."""
+    es, ev = _stages(api, oracle_mod, W.c1(), seed=3)
+    assert es <= TC_TOL and ev <= TC_TOL, (es, ev)
+
+
+@pytest.mark.parametrize("mk", ["plane", "cylinder"])
+def test_operator_tensor_cores(api, oracle_mod, mk):
+    w = W.c1() if mk == "plane" else W.small_cylinder(n_vox=10, n_angles=4, n_el=3)
+    taps = oracle_mod.taps_for(w)
+    plan = api.Plan(w, taps=taps, conv_tc=True)
+    x32 = w.x.astype(np.float32)
+    s = plan.forward(torch.from_numpy(x32).cuda()).cpu().numpy()
+    s_ref, _ = oracle_mod.forward(w, taps, x32.astype(np.float64))
+    assert rel(s, s_ref) <= TC_TOL, rel(s, s_ref)
+    y = np.random.default_rng(8).standard_normal(s.shape).astype(np.float32)
+    z = plan.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
+    z_ref, _ = oracle_mod.adjoint(w, taps, y.astype(np.float64))
+    assert rel(z, z_ref) <= TC_TOL, rel(z, z_ref)
+    # the FP32 / FP64-accumulation convolution of the plain plan agrees too
+    plain = api.Plan(w, taps=taps)
+    s2 = plain.forward(torch.from_numpy(x32).cuda()).cpu().numpy()
+    assert rel(s, s2) <= TC_TOL
+    assert plan.info["tc_error"] == 0 and api._lib.pat_plan_get_info(plan.handle)["tc_error"] == 0
+
+
+def test_dot_product_tensor_cores(api, oracle_mod):
+    w = W.small_cylinder(n_vox=8, n_angles=4, n_el=3)
+    plan = api.Plan(w, taps=oracle_mod.taps_for(w), conv_tc=True)
+    g = torch.Generator(device="cuda").manual_seed(1)
+    x = torch.randn(w.N, device="cuda", generator=g)
+    y = torch.randn(w.K, w.L, device="cuda", generator=g)
+    lhs = float((plan.forward(x).double() * y.double()).sum())
+    rhs = float((x.double() * plan.adjoint(y.contiguous()).double()).sum())
+    assert abs(lhs - rhs) <= TC_TOL * abs(lhs)
+
+
+def test_recon_with_tensor_core_plan(api, oracle_mod):
+    w = W.c1().with_(n=(8, 8, 8), origin=W.centred_origin((8, 8, 8), 0.1e-3))
+    taps = oracle_mod.taps_for(w)
+    plan = api.Plan(w, taps=taps, conv_tc=True)
+    xt = torch.from_numpy(W.uniform_phantom(512, 7)).cuda()
+    s = plan.forward(xt)
+    x0 = torch.zeros(512, device="cuda")
+    r0 = float((plan.forward(x0) - s).norm())
+    x30 = plan.recon(s, x0, iters=30, lambda_R=0.0)
+    r30 = float((plan.forward(x30) - s).norm())
+    assert float(x30.min()) >= 0.0 and r30 < 0.5 * r0
