@@ -59,7 +59,7 @@ enum { PAT_EIR_GAUSS_SINE = 0, PAT_EIR_BOX = 1 };
  *                        convolution then carries about 16 significant bits
  *                        per product instead of FP64 accumulation. */
 enum { PAT_FLAG_ALLOW_CLIP = 1, PAT_FLAG_CONV_TC = 2 };
-enum { PAT_OP_FORWARD = 1, PAT_OP_ADJOINT = 2, PAT_OP_RECON = 3 };
+enum { PAT_OP_FORWARD = 1, PAT_OP_ADJOINT = 2, PAT_OP_RECON = 3, PAT_OP_FORWARD_DC = 4 };
 
 /* Uniform voxel grid (Sec. 2.4): centres origin + pitch * (ix, iy, iz). */
 typedef struct pat_grid {
@@ -141,6 +141,14 @@ typedef struct pat_plan_info {
 pat_status pat_system_kernel(const pat_system *sys, double c, double fs, int32_t U, int32_t n_lo, int32_t n_taps,
                              double *taps_dev, void *stream);
 
+/* Derivative of the discrete system kernel with respect to the speed of
+ * sound, d h-bar[n] / dc for the same n as pat_system_kernel (Eq. def_bh with
+ * g(t) = -1/2 c t phi(|c t|) replaced by dg/dc = -1/2 t [phi + r phi'](|c t|);
+ * the triangle window D = 1/(U Fs) does not depend on c).  Same arguments,
+ * quadrature and errors as pat_system_kernel. */
+pat_status pat_system_kernel_dc(const pat_system *sys, double c, double fs, int32_t U, int32_t n_lo, int32_t n_taps,
+                                double *dtaps_dev, void *stream);
+
 /* Creates a plan: copies the grid, the K transducer descriptors (host array
  * tx[K]) and the taps (host array taps_host[n_taps], h-bar[n_lo + t]) to the
  * device, derives the per-element frames, and scans every voxel-transducer
@@ -188,6 +196,20 @@ pat_status pat_conv_forward(pat_plan *plan, const float *f, float *s, void *stre
 pat_status pat_conv_adjoint(pat_plan *plan, const float *s, float *v, void *stream);
 /* z[N] = transpose of the geometric assembly applied to v[K][U L] (Alg. 7 / Alg. 6). */
 pat_status pat_adjoint_geometric(pat_plan *plan, const float *v, float *z, void *ws, size_t ws_bytes, void *stream);
+
+/* ds = d(A x)/dc, the derivative of the forward operator with respect to the
+ * speed of sound c at the plan's c, for a fixed x (surface method).  c enters
+ * through the bin radii r = c tau (the swept areas: d|M|/dc = tau_e A'(r_e)
+ * at the two radii of a bin or group, with A' = dA/dr of Sec. 4), through the
+ * weights U Fs / (c tau) (Eq. ui_area) and through h-bar (dtaps, from
+ * pat_system_kernel_dc for the plan's tap window, device doubles[n_taps]).
+ * The bins of every pair stay those of the plan (the derivative of the
+ * piecewise-smooth operator between bin changes).  x: device float[N];
+ * ds: device float[K][L] (overwritten); ws: pat_workspace_bytes(plan,
+ * PAT_OP_FORWARD_DC) bytes.  PAT_ERR_UNSUPPORTED for the point method or when
+ * the doubled shared-memory windows do not fit. */
+pat_status pat_forward_dc(pat_plan *plan, const float *x, const double *dtaps, float *ds, void *ws, size_t ws_bytes,
+                          void *stream);
 
 /* Projected FISTA for the Tikhonov non-negative least squares problem of
  * Eq. (nnls_tik):  min_{p >= 0} 1/2 |A p - s|^2 + 1/2 lambda_R |p|^2.

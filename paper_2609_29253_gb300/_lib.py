@@ -17,7 +17,7 @@ from . import build as _build
 
 PAT_OK = 0
 PAT_ERR_WORKSPACE = 4
-PAT_OP_FORWARD, PAT_OP_ADJOINT, PAT_OP_RECON = 1, 2, 3
+PAT_OP_FORWARD, PAT_OP_ADJOINT, PAT_OP_RECON, PAT_OP_FORWARD_DC = 1, 2, 3, 4
 PAT_FLAG_ALLOW_CLIP = 1
 PAT_FLAG_CONV_TC = 2
 _STATUS = {0: "PAT_OK", 1: "PAT_ERR_INVALID_ARG", 2: "PAT_ERR_GEOMETRY", 3: "PAT_ERR_WINDOW",
@@ -52,9 +52,10 @@ class pat_plan_info(C.Structure):
                 ("tc_error", C.c_int64)]
 
 
-EXPORTS = ["pat_system_kernel", "pat_plan_create", "pat_plan_destroy", "pat_plan_get_info", "pat_workspace_bytes",
-           "pat_forward", "pat_adjoint", "pat_forward_geometric", "pat_conv_forward", "pat_conv_adjoint",
-           "pat_adjoint_geometric", "pat_recon", "pat_forward_static", "pat_last_error", "pat_version"]
+EXPORTS = ["pat_system_kernel", "pat_system_kernel_dc", "pat_plan_create", "pat_plan_destroy", "pat_plan_get_info",
+           "pat_workspace_bytes", "pat_forward", "pat_adjoint", "pat_forward_geometric", "pat_conv_forward",
+           "pat_conv_adjoint", "pat_adjoint_geometric", "pat_forward_dc", "pat_recon", "pat_forward_static",
+           "pat_last_error", "pat_version"]
 
 _lock = threading.Lock()
 _lib = None
@@ -78,6 +79,10 @@ def load(build_if_missing: bool = True):
         L.pat_system_kernel.restype = st
         L.pat_system_kernel.argtypes = [C.POINTER(pat_system), C.c_double, C.c_double, C.c_int32, C.c_int32,
                                         C.c_int32, vp, vp]
+        L.pat_system_kernel_dc.restype = st
+        L.pat_system_kernel_dc.argtypes = L.pat_system_kernel.argtypes
+        L.pat_forward_dc.restype = st
+        L.pat_forward_dc.argtypes = [vp, vp, vp, vp, vp, C.c_size_t, vp]
         L.pat_plan_create.restype = st
         L.pat_plan_create.argtypes = [C.POINTER(vp), C.POINTER(pat_grid), vp, C.c_int32, C.POINTER(pat_params),
                                       C.c_double, vp, C.c_int32, C.c_int32, vp]
@@ -129,6 +134,16 @@ def pat_system_kernel(rbf_kind, kappa, eir_kind, eir, c, fs, U, n_lo, taps_dev, 
     sys = pat_system(int(rbf_kind), int(eir_kind), float(kappa), (C.c_double * 4)(*[float(v) for v in eir]))
     check(load().pat_system_kernel(C.byref(sys), float(c), float(fs), int(U), int(n_lo), int(taps_dev.numel()),
                                    _ptr(taps_dev), _stream(stream)))
+
+
+def pat_system_kernel_dc(rbf_kind, kappa, eir_kind, eir, c, fs, U, n_lo, dtaps_dev, stream=None):
+    sys = pat_system(int(rbf_kind), int(eir_kind), float(kappa), (C.c_double * 4)(*[float(v) for v in eir]))
+    check(load().pat_system_kernel_dc(C.byref(sys), float(c), float(fs), int(U), int(n_lo), int(dtaps_dev.numel()),
+                                      _ptr(dtaps_dev), _stream(stream)))
+
+
+def pat_forward_dc(plan, x, dtaps, ds, ws, stream=None):
+    check(load().pat_forward_dc(plan, _ptr(x), _ptr(dtaps), _ptr(ds), _ptr(ws), ws.numel(), _stream(stream)))
 
 
 def pat_plan_create(n, origin, pitch, tx, c, fs, t0, L, U, dl, method, q1, q2, flags, kappa, taps, n_lo,

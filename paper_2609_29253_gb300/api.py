@@ -21,6 +21,14 @@ def system_taps(w: Workload, device=None) -> np.ndarray:
     return taps.cpu().numpy()
 
 
+def system_taps_dc(w: Workload, device=None) -> torch.Tensor:
+    """d h-bar / dc for the workload's tap window, computed on the GPU, FP64
+    (device tensor, the argument of Plan.forward_dc)."""
+    dtaps = torch.empty(w.T, dtype=torch.float64, device=device or "cuda")
+    _lib.pat_system_kernel_dc(w.rbf_kind, w.kappa, w.eir_kind, w.eir_par, w.c, w.fs, w.U, w.n_lo, dtaps)
+    return dtaps
+
+
 class Plan:
     """An operator A (and A^T) for one grid, one set of transducer positions
     and one time axis; see pat_plan_create in include/pat.h."""
@@ -100,6 +108,21 @@ class Plan:
         _lib.pat_conv_adjoint(self.handle, s, v)
         return v
 
+    def forward_dc(self, x: torch.Tensor, dtaps: torch.Tensor | None = None) -> torch.Tensor:
+        """d(A x)/dc at the plan's speed of sound (see pat_forward_dc)."""
+        x = self._f32(x, self.N)
+        if dtaps is None:
+            dtaps = self._dtaps()
+        ds = torch.empty((self.K, self.L), dtype=torch.float32, device=self.device)
+        _lib.pat_forward_dc(self.handle, x, dtaps, ds, self.workspace(_lib.PAT_OP_FORWARD_DC))
+        return ds
+
+    def _dtaps(self) -> torch.Tensor:
+        if getattr(self, "_dtaps_t", None) is None:
+            with torch.cuda.device(self.device):
+                self._dtaps_t = system_taps_dc(self.w, self.device)
+        return self._dtaps_t
+
     def recon(self, s: torch.Tensor, x0: torch.Tensor | None = None, iters: int = 50, lambda_R: float = 0.0,
               step: float = 0.0) -> torch.Tensor:
         """Projected FISTA for Eq. (nnls_tik); step <= 0 estimates 1/|A^T A + lambda|."""
@@ -126,8 +149,36 @@ class PatForward(torch.autograd.Function):
         return ctx.plan.adjoint(gs.contiguous()), None
 
 
-def forward(plan: Plan, x: torch.Tensor) -> torch.Tensor:
-    return PatForward.apply(x, plan)
+class PatForwardSpeed(torch.autograd.Function):
+    """s = A(c) x with gradients for x (A^T, App. G) and for the speed of
+    sound c (the scalar <ds, dA/dc x>, pat_forward_dc).  c is a 0-d tensor
+    equal to the plan's speed of sound; the plan fixes the bins."""
+
+    @staticmethod
+    def forward(ctx, x, c, plan):
+        if abs(float(c) - plan.w.c) > 1e-9 * plan.w.c:
+            raise ValueError(f"c = {float(c)} differs from the plan's {plan.w.c}: build a plan at this c")
+        ctx.plan = plan
+        ctx.save_for_backward(x)
+        return plan.forward(x.contiguous())
+
+    @staticmethod
+    def backward(ctx, gs):
+        (x,) = ctx.saved_tensors
+        gs = gs.contiguous()
+        gx = ctx.plan.adjoint(gs) if ctx.needs_input_grad[0] else None
+        gc = None
+        if ctx.needs_input_grad[1]:
+            ds = ctx.plan.forward_dc(x.detach().contiguous())
+            gc = (gs.double() * ds.double()).sum().to(torch.float32)
+        return gx, gc, None
+
+
+def forward(plan: Plan, x: torch.Tensor, c: torch.Tensor | None = None) -> torch.Tensor:
+    """s = A x; with c (a 0-d tensor) the speed of sound is differentiable too."""
+    if c is None:
+        return PatForward.apply(x, plan)
+    return PatForwardSpeed.apply(x, c, plan)
 
 
 def adjoint(plan: Plan, s: torch.Tensor) -> torch.Tensor:

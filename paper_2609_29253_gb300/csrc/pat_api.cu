@@ -87,6 +87,24 @@ extern "C" pat_status pat_system_kernel(const pat_system *sys, double c, double 
     return PAT_OK;
 }
 
+extern "C" pat_status pat_system_kernel_dc(const pat_system *sys, double c, double fs, int32_t U, int32_t n_lo,
+                                           int32_t n_taps, double *dtaps_dev, void *stream)
+{
+    g_err.clear();
+    if (!sys || !dtaps_dev) return fail(PAT_ERR_INVALID_ARG, "pat_system_kernel_dc: null pointer");
+    if (n_taps < 1 || U < 1 || !(c > 0) || !(fs > 0) || !(sys->kappa > 0) || !(sys->eir[3] > 0))
+        return fail(PAT_ERR_INVALID_ARG, "pat_system_kernel_dc: sizes and parameters must be positive");
+    if (sys->rbf_kind < PAT_RBF_BUMP || sys->rbf_kind > PAT_RBF_WENDLAND)
+        return fail(PAT_ERR_INVALID_ARG, "pat_system_kernel_dc: unknown rbf_kind %d", sys->rbf_kind);
+    if (sys->eir_kind != PAT_EIR_GAUSS_SINE && sys->eir_kind != PAT_EIR_BOX)
+        return fail(PAT_ERR_INVALID_ARG, "pat_system_kernel_dc: unknown eir_kind %d", sys->eir_kind);
+    if (sys->eir_kind == PAT_EIR_GAUSS_SINE && !(sys->eir[1] > 0))
+        return fail(PAT_ERR_INVALID_ARG, "pat_system_kernel_dc: Gaussian width must be positive");
+    CK(launch_taps(sys->rbf_kind, sys->eir_kind, sys->kappa, c, sys->eir, (double)U * fs, n_lo, n_taps, dtaps_dev,
+                   (cudaStream_t)stream, true));
+    return PAT_OK;
+}
+
 // ---------------------------------------------------------------------------
 static pat_status validate(const pat_grid *grid, const pat_transducer *tx, int K, const pat_params *p, double kappa,
                            const double *taps, int n_taps)
@@ -164,6 +182,7 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
     tm.deltad = params->c / tm.ufs;
     tm.deltaf = (float)tm.deltad;
     tm.ufsf = (float)tm.ufs;
+    tm.invcf = (float)(1.0 / params->c);
     auto split = [](double v) {
         float hi = (float)v;
         return make_float2(hi, (float)(v - (double)hi));
@@ -399,6 +418,7 @@ static size_t ws_P(const pat_plan *p) { return align256(sizeof(float2) * (size_t
 static size_t ws_f(const pat_plan *p) { return p->tc ? align256(sizeof(float) * (size_t)p->tm.UL * p->K) : 0; }
 static size_t ws_fwd(const pat_plan *p) { return ws_D(p) + ws_f(p); }
 static size_t ws_adj(const pat_plan *p) { return ws_P(p) + ws_f(p); }
+static size_t ws_fwd_dc(const pat_plan *p) { return 2 * ws_D(p); }
 static size_t ws_recon(const pat_plan *p)
 {
     return std::max(ws_fwd(p), ws_adj(p)) + align256(sizeof(float) * (size_t)p->K * p->tm.L) +
@@ -411,6 +431,7 @@ extern "C" size_t pat_workspace_bytes(const pat_plan *p, int32_t op)
     if (op == PAT_OP_FORWARD) return ws_fwd(p);
     if (op == PAT_OP_ADJOINT) return ws_adj(p);
     if (op == PAT_OP_RECON) return ws_recon(p);
+    if (op == PAT_OP_FORWARD_DC) return ws_fwd_dc(p);
     return 0;
 }
 
@@ -516,6 +537,31 @@ extern "C" pat_status pat_adjoint_geometric(pat_plan *p, const float *v, float *
     pat_status st = check_ws(p, ws, ws_bytes, ws_adj(p), "pat_adjoint_geometric");
     if (st != PAT_OK) return st;
     return enqueue_adjoint(p, v, 1, z, ws, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// speed-of-sound derivative of s = A x
+// ---------------------------------------------------------------------------
+extern "C" pat_status pat_forward_dc(pat_plan *p, const float *x, const double *dtaps, float *ds, void *ws,
+                                     size_t ws_bytes, void *stream)
+{
+    g_err.clear();
+    if (!p || !x || !dtaps || !ds) return fail(PAT_ERR_INVALID_ARG, "pat_forward_dc: null pointer");
+    if (p->tm.method != PAT_METHOD_SURFACE)
+        return fail(PAT_ERR_UNSUPPORTED, "pat_forward_dc: only the surface method (closed-form areas)");
+    const size_t need4 = 4 * sizeof(float) * (size_t)p->fwd_span;
+    const size_t need_epi = sizeof(float) * (size_t)(2 * p->tm.UL + 2 * p->nW);
+    if (need4 > (size_t)p->smem_optin || need_epi > (size_t)p->smem_optin)
+        return fail(PAT_ERR_UNSUPPORTED, "pat_forward_dc: needs %zu bytes of shared memory per block, device has %d",
+                    std::max(need4, need_epi), p->smem_optin);
+    pat_status st = check_ws(p, ws, ws_bytes, ws_fwd_dc(p), "pat_forward_dc");
+    if (st != PAT_OK) return st;
+    cudaStream_t cs = (cudaStream_t)stream;
+    double *Dg = (double *)ws, *Dd = (double *)((char *)ws + ws_D(p));
+    CK(launch_fwd_geom_dc(p->tx, p->K, p->kind_all, p->tm, p->g, x, Dg, Dd, p->fwd_chunks, p->fwd_base, p->fwd_span,
+                          cs));
+    CK(launch_fwd_dc_epilogue(Dg, Dd, p->W, dtaps, p->T, p->nW, p->n_lo, p->tm, p->K, ds, cs));
+    return PAT_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -185,7 +185,7 @@ struct BinWindow {
 struct FwdSurfaceSink {
     BinWindow w;
     float x, prev;
-    __device__ __forceinline__ void group(int e0, int, float val)
+    __device__ __forceinline__ void group(int e0, int, float val, float)
     {
         const float v = x * val;
         const float2 dv = ff_two_sum(v, -prev); // exact difference of consecutive group values
@@ -195,6 +195,27 @@ struct FwdSurfaceSink {
     __device__ __forceinline__ void finish(int end)
     {
         if (prev != 0.f) acc2(w.hi, w.lo, w.idx(end), -prev, 0.f);
+    }
+};
+
+// Forward sink of the speed-of-sound derivative: the per-bin shares and their
+// c-derivatives, each into its own compensated difference array.
+struct FwdDerivSink {
+    BinWindow w, wd;
+    float x, prev, dprev;
+    __device__ __forceinline__ void group(int e0, int, float val, float dval)
+    {
+        const float v = x * val, dv = x * dval;
+        const float2 a = ff_two_sum(v, -prev), b = ff_two_sum(dv, -dprev);
+        if (a.x != 0.f) acc2(w.hi, w.lo, w.idx(e0), a.x, a.y);
+        if (b.x != 0.f) acc2(wd.hi, wd.lo, wd.idx(e0), b.x, b.y);
+        prev = v;
+        dprev = dv;
+    }
+    __device__ __forceinline__ void finish(int end)
+    {
+        if (prev != 0.f) acc2(w.hi, w.lo, w.idx(end), -prev, 0.f);
+        if (dprev != 0.f) acc2(wd.hi, wd.lo, wd.idx(end), -dprev, 0.f);
     }
 };
 
@@ -242,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, 4) fwd_geom_kernel(const TxDev *__re
                 point_pair<KIND>(t, tm, ix, iy, iz, s);
             } else {
                 FwdSurfaceSink s{win, xv, 0.f};
-                surface_pair<KIND>(t, tm, ix, iy, iz, s, glx, glw);
+                surface_pair<KIND, false>(t, tm, ix, iy, iz, s, glx, glw);
             }
         }
         __syncwarp();
@@ -256,6 +277,57 @@ __global__ void __launch_bounds__(kThreads, 4) fwd_geom_kernel(const TxDev *__re
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
             const double v = (double)win.hi[i] + (double)win.lo[i];
             if (v != 0.0) atomicAdd(&row[i], v);
+        }
+    }
+}
+
+// Speed-of-sound derivative of the geometric assembly: the difference arrays
+// of f (Dg) and of its c-derivative at fixed bins (Dd), same layout and
+// window as fwd_geom_kernel (four window arrays in shared memory).
+template <int KIND>
+__global__ void __launch_bounds__(kThreads) fwd_geom_dc_kernel(const TxDev *__restrict__ tx, TimeDev tm, GridDev g,
+                                                               const float *__restrict__ x, double *__restrict__ Dg,
+                                                               double *__restrict__ Dd, int bricks_per_cta,
+                                                               const int *__restrict__ base, int span)
+{
+    extern __shared__ float sD[];
+    __shared__ float glx[kGLTable], glw[kGLTable];
+    const int k = blockIdx.y;
+    const int n = tm.UL + 1;
+    BinWindow win, wind;
+    win.hi = sD;
+    win.lo = sD + span;
+    wind.hi = sD + 2 * span;
+    wind.lo = sD + 3 * span;
+    win.base = wind.base = base[k];
+    win.top = wind.top = min(tm.UL, win.base + span - 1);
+    for (int b = threadIdx.x; b < 4 * span; b += blockDim.x) sD[b] = 0.f;
+    gl_fill(glx, glw, threadIdx.x);
+    __syncthreads();
+    const TxDev &t = tx[k];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    long long b0 = (long long)blockIdx.x * bricks_per_cta;
+    long long b1 = min(b0 + bricks_per_cta, g.nbricks);
+    for (long long br = b0 + warp; br < b1; br += kWarpsPerBlock) {
+        int ix, iy, iz;
+        if (brick_voxel(g, br, lane, ix, iy, iz)) {
+            FwdDerivSink s{win, wind, x[((long long)iz * g.ny + iy) * g.nx + ix], 0.f, 0.f};
+            surface_pair<KIND, true>(t, tm, ix, iy, iz, s, glx, glw);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    const int m = win.top - win.base + 1;
+    double *row = Dg + (size_t)k * n + win.base, *rowd = Dd + (size_t)k * n + win.base;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const double v = (double)win.hi[i] + (double)win.lo[i];
+        const double vd = (double)wind.hi[i] + (double)wind.lo[i];
+        if (gridDim.x == 1) {
+            row[i] = v;
+            rowd[i] = vd;
+        } else {
+            if (v != 0.0) atomicAdd(&row[i], v);
+            if (vd != 0.0) atomicAdd(&rowd[i], vd);
         }
     }
 }
@@ -348,6 +420,61 @@ __global__ void __launch_bounds__(kThreads) fwd_epilogue_kernel(const void *__re
     if (s) conv_down(f, W, nW, n_lo, tm, s + (size_t)k * tm.L);
 }
 
+// ds/dc = downsample_U(h-bar * f' + (dh-bar/dc) * f) with f' the c-derivative
+// of f: f'[b] = prefix(Dd)[b] w_b - f[b] / c (the weight U Fs / (c tau) also
+// depends on c).  Dg, Dd: difference arrays [K][UL + 1]; dtaps: dh-bar/dc,
+// T doubles, combined with the U-box like W.
+__global__ void __launch_bounds__(kThreads) fwd_dc_epilogue_kernel(const double *__restrict__ Dg,
+                                                                   const double *__restrict__ Dd,
+                                                                   const float *__restrict__ Wg,
+                                                                   const double *__restrict__ dtaps, int T, int nW,
+                                                                   int n_lo, TimeDev tm, float *__restrict__ ds)
+{
+    extern __shared__ float sm[];
+    __shared__ double tmp[kWarpsPerBlock];
+    float *f = sm, *fd = sm + tm.UL, *W = sm + 2 * tm.UL, *Wc = W + nW;
+    const int k = blockIdx.x, UL = tm.UL, U = tm.U;
+    for (int j = threadIdx.x; j < nW; j += blockDim.x) {
+        W[j] = Wg[j];
+        double acc = 0.0;
+        for (int u = 0; u < U; ++u) {
+            const int t = j - (U - 1) + u;
+            if (t >= 0 && t < T) acc += dtaps[t];
+        }
+        Wc[j] = (float)(acc / U);
+    }
+    const double *drow = Dg + (size_t)k * (UL + 1), *ddrow = Dd + (size_t)k * (UL + 1);
+    const int chunk = (UL + blockDim.x - 1) / blockDim.x;
+    const int c0 = min(UL, (int)threadIdx.x * chunk), c1 = min(UL, c0 + chunk);
+    double part = 0.0, partd = 0.0;
+    for (int b = c0; b < c1; ++b) {
+        part += drow[b];
+        partd += ddrow[b];
+    }
+    double run = block_exclusive_scan(part, tmp);
+    double rund = block_exclusive_scan(partd, tmp);
+    for (int b = c0; b < c1; ++b) {
+        run += drow[b];
+        rund += ddrow[b];
+        const double wb = bin_weight(tm, b);
+        f[b] = (float)(run * wb);
+        fd[b] = (float)(rund * wb - run * wb / tm.c);
+    }
+    __syncthreads();
+    float *out = ds + (size_t)k * tm.L;
+    for (int l = threadIdx.x; l < tm.L; l += blockDim.x) {
+        const long long bs = (long long)U * l - n_lo + U - 1;
+        const int j0 = (int)max(0LL, bs - (UL - 1));
+        const int j1 = (int)min((long long)nW - 1, bs);
+        double acc = 0.0;
+        for (int j = j0; j <= j1; ++j) {
+            acc = fma((double)W[j], (double)fd[bs - j], acc);
+            acc = fma((double)Wc[j], (double)f[bs - j], acc);
+        }
+        out[l] = (float)acc;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // adjoint: v = h-bar^- * upsample^T(s); mode 0: P[b] = sum_{b'<b} wgt v (float2
 // hi/lo), mode 1: w = U Fs v (point method), mode 2: v itself.
@@ -416,7 +543,7 @@ struct AdjSurfaceSink {
     float2 pe;  // P at the current group start
     bool have;
     __device__ __forceinline__ int clampi(int e) const { return min(max(e, 0), UL); }
-    __device__ __forceinline__ void group(int e0, int e1, float val)
+    __device__ __forceinline__ void group(int e0, int e1, float val, float)
     {
         if (!have) {
             pe = __ldg(&P[clampi(e0)]);
@@ -463,7 +590,7 @@ __global__ void __launch_bounds__(kThreads, 4) adj_geom_kernel(const TxDev *__re
                 acc += (double)s.acc;
             } else {
                 AdjSurfaceSink s{(const float2 *)Pv + (size_t)k * stride, tm.UL, 0.f, make_float2(0.f, 0.f), false};
-                surface_pair<KIND>(t, tm, ix, iy, iz, s, glx, glw);
+                surface_pair<KIND, false>(t, tm, ix, iy, iz, s, glx, glw);
                 acc += (double)s.acc;
             }
         }
@@ -496,6 +623,18 @@ __device__ double rbf_dev(int kind, double kappa, double r)
     return (1.0 - q) * (1.0 - q);
 }
 
+// d(r phi(r))/dr, the radial factor of dg/dc: g(t) = -1/2 c t phi(|c t|) gives
+// dg/dc = -1/2 t [phi(rho) + rho phi'(rho)], rho = |c t|.
+__device__ double rbf_dc_dev(int kind, double kappa, double r)
+{
+    r = fabs(r);
+    if (r >= kappa) return 0.0;
+    double q = r / kappa;
+    if (kind == PAT_RBF_BUMP) return (1.0 - q * q) * (1.0 - 5.0 * q * q);
+    if (kind == PAT_RBF_CONE) return 1.0 - 2.0 * q;
+    return (1.0 - q) * (1.0 - 3.0 * q);
+}
+
 __device__ double eir_dev(const SysDev &sy, double t)
 {
     if (t < 0.0 || t > sy.e[3]) return 0.0;
@@ -506,7 +645,8 @@ __device__ double eir_dev(const SysDev &sy, double t)
     return sy.e[0];
 }
 
-__device__ double h_dev(const SysDev &sy, const double *gx, const double *gw, double t)
+// h(t) = (e * g)(t); with dc, (e * dg/dc)(t) instead.
+__device__ double h_dev(const SysDev &sy, const double *gx, const double *gw, double t, bool dc = false)
 {
     // pieces of [max(0, t - k/c), min(Te, t + k/c)] split at t (kink of g at 0)
     const double kc = sy.kappa / sy.c;
@@ -528,14 +668,16 @@ __device__ double h_dev(const SysDev &sy, const double *gx, const double *gw, do
             for (int i = 0; i < kGL; ++i) {
                 double tp = m + 0.5 * wdt * gx[i];
                 double ct = sy.c * (t - tp);
-                acc += 0.5 * wdt * gw[i] * eir_dev(sy, tp) * (-0.5 * ct * rbf_dev(sy.rbf, sy.kappa, ct));
+                const double g = dc ? -0.5 * (t - tp) * rbf_dc_dev(sy.rbf, sy.kappa, ct)
+                                    : -0.5 * ct * rbf_dev(sy.rbf, sy.kappa, ct);
+                acc += 0.5 * wdt * gw[i] * eir_dev(sy, tp) * g;
             }
         }
     }
     return acc;
 }
 
-__global__ void taps_kernel(SysDev sy, double ufs, int n_lo, int T, double *__restrict__ taps)
+__global__ void taps_kernel(SysDev sy, double ufs, int n_lo, int T, double *__restrict__ taps, bool dc)
 {
     __shared__ double gx[kGL], gw[kGL];
     if (threadIdx.x < kGL) {
@@ -588,7 +730,7 @@ __global__ void taps_kernel(SysDev sy, double ufs, int n_lo, int T, double *__re
             double m = lo + (q + 0.5) * wdt;
             for (int i = 0; i < kGL; ++i) {
                 double sv = m + 0.5 * wdt * gx[i];
-                acc += 0.5 * wdt * gw[i] * (D - fabs(sv)) * h_dev(sy, gx, gw, nD + sv);
+                acc += 0.5 * wdt * gw[i] * (D - fabs(sv)) * h_dev(sy, gx, gw, nD + sv, dc);
             }
         }
     }
@@ -708,6 +850,40 @@ cudaError_t launch_fwd_geom(const TxDev *tx, int K, int kind, const TimeDev &tm,
     return fwd_geom_go<PAT_METHOD_SURFACE, kKindAny>(grid, smem, st, tx, tm, g, x, Dg, b, base, span);
 }
 
+cudaError_t launch_fwd_geom_dc(const TxDev *tx, int K, int kind, const TimeDev &tm, const GridDev &g, const float *x,
+                               double *Dg, double *Dd, int chunks, const int *base, int span, cudaStream_t st)
+{
+    size_t smem = 4 * sizeof(float) * (size_t)span;
+    long long bpc = (g.nbricks + chunks - 1) / chunks;
+    bpc = ((bpc + kWarpsPerBlock - 1) / kWarpsPerBlock) * kWarpsPerBlock;
+    unsigned gx = (unsigned)((g.nbricks + bpc - 1) / bpc);
+    const size_t bytes = sizeof(double) * (size_t)(tm.UL + 1) * K;
+    cudaError_t e = cudaMemsetAsync(Dg, 0, bytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(Dd, 0, bytes, st);
+    if (e != cudaSuccess) return e;
+    const dim3 grid(gx, (unsigned)K);
+    const void *fn = kind == PAT_PLANE      ? (const void *)fwd_geom_dc_kernel<PAT_PLANE>
+                     : kind == PAT_CYLINDER ? (const void *)fwd_geom_dc_kernel<PAT_CYLINDER>
+                                            : (const void *)fwd_geom_dc_kernel<kKindAny>;
+    set_smem_attr(fn, smem);
+    if (kind == PAT_PLANE)
+        fwd_geom_dc_kernel<PAT_PLANE><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, Dd, (int)bpc, base, span);
+    else if (kind == PAT_CYLINDER)
+        fwd_geom_dc_kernel<PAT_CYLINDER><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, Dd, (int)bpc, base, span);
+    else
+        fwd_geom_dc_kernel<kKindAny><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, Dd, (int)bpc, base, span);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_dc_epilogue(const double *Dg, const double *Dd, const float *W, const double *dtaps, int T,
+                                   int nW, int n_lo, const TimeDev &tm, int K, float *ds, cudaStream_t st)
+{
+    size_t smem = sizeof(float) * (size_t)(2 * tm.UL + 2 * nW);
+    set_smem_attr((const void *)fwd_dc_epilogue_kernel, smem);
+    fwd_dc_epilogue_kernel<<<K, kThreads, smem, st>>>(Dg, Dd, W, dtaps, T, nW, n_lo, tm, ds);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fwd_epilogue(const void *in, int in_stride, const float *W, int nW, int n_lo, const TimeDev &tm,
                                 int mode, int K, float *s, float *f_out, cudaStream_t st)
 {
@@ -745,7 +921,7 @@ cudaError_t launch_adj_geom(const TxDev *tx, int K, int kind, const TimeDev &tm,
 }
 
 cudaError_t launch_taps(int rbf, int eir, double kappa, double c, const double *e, double ufs, int n_lo, int T,
-                        double *taps, cudaStream_t st)
+                        double *taps, cudaStream_t st, bool dc)
 {
     SysDev sy;
     sy.rbf = rbf;
@@ -753,7 +929,7 @@ cudaError_t launch_taps(int rbf, int eir, double kappa, double c, const double *
     sy.kappa = kappa;
     sy.c = c;
     for (int i = 0; i < 4; ++i) sy.e[i] = e[i];
-    taps_kernel<<<(T + 63) / 64, 64, 0, st>>>(sy, ufs, n_lo, T, taps);
+    taps_kernel<<<(T + 63) / 64, 64, 0, st>>>(sy, ufs, n_lo, T, taps, dc);
     return cudaGetLastError();
 }
 

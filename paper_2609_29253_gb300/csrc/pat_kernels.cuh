@@ -28,8 +28,14 @@ cudaError_t launch_adj_conv(const float *in, int from_v, const float *W, int nW,
                             int K, void *out, cudaStream_t st);
 cudaError_t launch_adj_geom(const TxDev *tx, int K, int kind, const TimeDev &tm, const GridDev &g, const void *P,
                             float *z, cudaStream_t st);
+// dc: dh-bar/dc instead of h-bar
 cudaError_t launch_taps(int rbf, int eir, double kappa, double c, const double *e, double ufs, int n_lo, int T,
-                        double *taps, cudaStream_t st);
+                        double *taps, cudaStream_t st, bool dc = false);
+// speed-of-sound derivative: difference arrays of f and of df/dc (fixed bins)
+cudaError_t launch_fwd_geom_dc(const TxDev *tx, int K, int kind, const TimeDev &tm, const GridDev &g, const float *x,
+                               double *Dg, double *Dd, int chunks, const int *base, int span, cudaStream_t st);
+cudaError_t launch_fwd_dc_epilogue(const double *Dg, const double *Dd, const float *W, const double *dtaps, int T,
+                                   int nW, int n_lo, const TimeDev &tm, int K, float *ds, cudaStream_t st);
 cudaError_t launch_combine_taps(const double *taps, int T, int U, float *W, cudaStream_t st);
 cudaError_t launch_sub(const float *a, const float *b, float *o, long long n, cudaStream_t st);
 cudaError_t launch_fista(float *y, const float *g, float *xo, long long n, float step, float lam, float mom,
