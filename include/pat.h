@@ -59,7 +59,7 @@ enum { PAT_EIR_GAUSS_SINE = 0, PAT_EIR_BOX = 1 };
  *                        convolution then carries about 16 significant bits
  *                        per product instead of FP64 accumulation. */
 enum { PAT_FLAG_ALLOW_CLIP = 1, PAT_FLAG_CONV_TC = 2 };
-enum { PAT_OP_FORWARD = 1, PAT_OP_ADJOINT = 2, PAT_OP_RECON = 3, PAT_OP_FORWARD_DC = 4 };
+enum { PAT_OP_FORWARD = 1, PAT_OP_ADJOINT = 2, PAT_OP_RECON = 3, PAT_OP_FORWARD_DC = 4, PAT_OP_AUTOTUNE = 5 };
 
 /* Uniform voxel grid (Sec. 2.4): centres origin + pitch * (ix, iy, iz). */
 typedef struct pat_grid {
@@ -217,9 +217,37 @@ pat_status pat_forward_dc(pat_plan *plan, const float *x, const double *dtaps, f
  * step <= 0 estimates 1 / |A^T A + lambda_R| by 20 power iterations.
  * ws: pat_workspace_bytes(plan, PAT_OP_RECON) bytes.  Enqueues 2 operator
  * applications per iteration; synchronises `stream` only for the step
- * estimate. */
+ * estimate.  The FISTA scalars live on the device, so every iteration is the
+ * same launch sequence: on a capturable stream (not the legacy default
+ * stream, not one the caller is capturing) with iters >= 2 it is captured
+ * once into a CUDA graph and the graph is launched iters times; otherwise the
+ * launches are enqueued directly (same arithmetic). */
 pat_status pat_recon(pat_plan *plan, const float *s, float *x, int32_t iters, float lambda_R, float step, void *ws,
                      size_t ws_bytes, void *stream);
+
+/* pat_recon for nprob independent problems of any sizes (one plan each,
+ * distinct plans): arrays of nprob plans, measurements s[i], solutions x[i]
+ * (initial guesses in), lambda_R[i], step[i] (NULL or <= 0: estimated per
+ * problem), workspaces ws[i] of ws_bytes[i] >= pat_workspace_bytes(plans[i],
+ * PAT_OP_RECON).  On a capturable stream one iteration of every problem is
+ * captured into one CUDA graph, each problem on its own branch (fork and join
+ * on internal streams), so small problems overlap on the GPU; the graph is
+ * launched iters times.  Results equal those of pat_recon per problem.
+ * Synchronises `stream` for the step estimates only. */
+pat_status pat_recon_batch(pat_plan *const *plans, int32_t nprob, const float *const *s, float *const *x,
+                           int32_t iters, const float *lambda_R, const float *step, void *const *ws,
+                           const size_t *ws_bytes, void *stream);
+
+/* Autotuner of the launch shapes of one plan: times the forward geometric
+ * kernel with c0/4 .. 4 c0 CTAs per transducer (c0 the plan's default) and
+ * the adjoint gather with 2, 4 and 8 voxel bricks per CTA, each three times
+ * (the first run discarded) on x (device float[N]) and ws
+ * (pat_workspace_bytes(plan, PAT_OP_AUTOTUNE) bytes, contents overwritten),
+ * and keeps the fastest pair for later calls (pat_plan_info fwd_blocks and
+ * adj_blocks report it).  Costs about 13 operator halves; synchronises
+ * `stream`, which must not be under capture.  Results of later calls differ
+ * from the untuned ones only by the order of floating-point additions. */
+pat_status pat_plan_autotune(pat_plan *plan, const float *x, void *ws, size_t ws_bytes, void *stream);
 
 /* s = A x like pat_forward, for callers that cannot allocate device memory
  * (for example code running where cudaMalloc is forbidden or unavailable,

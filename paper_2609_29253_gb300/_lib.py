@@ -17,7 +17,7 @@ from . import build as _build
 
 PAT_OK = 0
 PAT_ERR_WORKSPACE = 4
-PAT_OP_FORWARD, PAT_OP_ADJOINT, PAT_OP_RECON, PAT_OP_FORWARD_DC = 1, 2, 3, 4
+PAT_OP_FORWARD, PAT_OP_ADJOINT, PAT_OP_RECON, PAT_OP_FORWARD_DC, PAT_OP_AUTOTUNE = 1, 2, 3, 4, 5
 PAT_FLAG_ALLOW_CLIP = 1
 PAT_FLAG_CONV_TC = 2
 _STATUS = {0: "PAT_OK", 1: "PAT_ERR_INVALID_ARG", 2: "PAT_ERR_GEOMETRY", 3: "PAT_ERR_WINDOW",
@@ -54,8 +54,8 @@ class pat_plan_info(C.Structure):
 
 EXPORTS = ["pat_system_kernel", "pat_system_kernel_dc", "pat_plan_create", "pat_plan_destroy", "pat_plan_get_info",
            "pat_workspace_bytes", "pat_forward", "pat_adjoint", "pat_forward_geometric", "pat_conv_forward",
-           "pat_conv_adjoint", "pat_adjoint_geometric", "pat_forward_dc", "pat_recon", "pat_forward_static",
-           "pat_last_error", "pat_version"]
+           "pat_conv_adjoint", "pat_adjoint_geometric", "pat_forward_dc", "pat_recon", "pat_recon_batch",
+           "pat_plan_autotune", "pat_forward_static", "pat_last_error", "pat_version"]
 
 _lock = threading.Lock()
 _lib = None
@@ -102,6 +102,10 @@ def load(build_if_missing: bool = True):
         L.pat_forward_static.argtypes = [vp, vp, vp, vp]
         L.pat_recon.restype = st
         L.pat_recon.argtypes = [vp, vp, vp, C.c_int32, C.c_float, C.c_float, vp, C.c_size_t, vp]
+        L.pat_recon_batch.restype = st
+        L.pat_recon_batch.argtypes = [vp, C.c_int32, vp, vp, C.c_int32, vp, vp, vp, vp, vp]
+        L.pat_plan_autotune.restype = st
+        L.pat_plan_autotune.argtypes = [vp, vp, vp, C.c_size_t, vp]
         L.pat_last_error.restype = C.c_char_p
         L.pat_last_error.argtypes = []
         L.pat_version.restype = C.c_int32
@@ -202,6 +206,22 @@ def pat_conv_adjoint(plan, s, v, stream=None):
 def pat_recon(plan, s, x, iters, lambda_R, step, ws, stream=None):
     check(load().pat_recon(plan, _ptr(s), _ptr(x), int(iters), float(lambda_R), float(step), _ptr(ws), ws.numel(),
                            _stream(stream)))
+
+
+def pat_recon_batch(plans, s_list, x_list, iters, lambdas, steps, ws_list, stream=None):
+    n = len(plans)
+    P = (C.c_void_p * n)(*[p.value if isinstance(p, C.c_void_p) else p for p in plans])
+    S = (C.c_void_p * n)(*[t.data_ptr() for t in s_list])
+    X = (C.c_void_p * n)(*[t.data_ptr() for t in x_list])
+    lam = (C.c_float * n)(*[float(v) for v in lambdas])
+    stp = (C.c_float * n)(*[float(v) for v in steps]) if steps is not None else None
+    WS = (C.c_void_p * n)(*[t.data_ptr() for t in ws_list])
+    WB = (C.c_size_t * n)(*[t.numel() for t in ws_list])
+    check(load().pat_recon_batch(P, n, S, X, int(iters), lam, stp, WS, WB, _stream(stream)))
+
+
+def pat_plan_autotune(plan, x, ws, stream=None):
+    check(load().pat_plan_autotune(plan, _ptr(x), _ptr(ws), ws.numel(), _stream(stream)))
 
 
 def pat_forward_static(plan, x, s, stream=None):

@@ -117,6 +117,13 @@ class Plan:
         _lib.pat_forward_dc(self.handle, x, dtaps, ds, self.workspace(_lib.PAT_OP_FORWARD_DC))
         return ds
 
+    def autotune(self, x: torch.Tensor | None = None) -> dict:
+        """Pick the fastest launch shapes for this plan (pat_plan_autotune)."""
+        x = self._f32(x, self.N) if x is not None else torch.ones(self.N, dtype=torch.float32, device=self.device)
+        _lib.pat_plan_autotune(self.handle, x, self.workspace(_lib.PAT_OP_AUTOTUNE))
+        self.info = _lib.pat_plan_get_info(self.handle)
+        return {"fwd_blocks": self.info["fwd_blocks"], "adj_blocks": self.info["adj_blocks"]}
+
     def _dtaps(self) -> torch.Tensor:
         if getattr(self, "_dtaps_t", None) is None:
             with torch.cuda.device(self.device):
@@ -130,6 +137,19 @@ class Plan:
         x = x0.clone() if x0 is not None else torch.zeros(self.N, dtype=torch.float32, device=self.device)
         _lib.pat_recon(self.handle, s, x, iters, lambda_R, step, self.workspace(_lib.PAT_OP_RECON))
         return x
+
+
+def recon_batch(plans: list, s_list: list, x0_list: list | None = None, iters: int = 50, lambdas=None,
+                steps=None) -> list:
+    """Projected FISTA for several independent problems (pat_recon_batch):
+    one CUDA graph per iteration of all problems, each on its own branch."""
+    xs = [x0.clone() if x0 is not None else torch.zeros(p.N, dtype=torch.float32, device=p.device)
+          for p, x0 in zip(plans, x0_list or [None] * len(plans))]
+    s_list = [p._f32(s, p.K * p.L) for p, s in zip(plans, s_list)]
+    ws = [p.workspace(_lib.PAT_OP_RECON) for p in plans]
+    lambdas = lambdas if lambdas is not None else [0.0] * len(plans)
+    _lib.pat_recon_batch([p.handle for p in plans], s_list, xs, iters, lambdas, steps, ws)
+    return xs
 
 
 def plan_from_workload(w: Workload, **kw) -> Plan:

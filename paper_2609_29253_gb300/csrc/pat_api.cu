@@ -28,7 +28,8 @@ struct pat_plan {
     double *taps;
     float *W;
     int T, nW, n_lo;
-    int fwd_chunks;
+    int fwd_chunks; // CTAs per transducer of the forward geometric kernel
+    int adj_wpb;    // warps (voxel bricks) per CTA of the adjoint gather
     int *fwd_base;  // per transducer: first fine-bin edge of its window
     int fwd_span;   // window length (edges) common to all transducers
     int smem_optin;
@@ -346,8 +347,9 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
         long long want = (8LL * std::max(sms, 1) + K - 1) / K;
         long long maxc = std::max(1LL, g.nbricks / kWarpsPerBlock);
         p->fwd_chunks = (int)std::max(1LL, std::min(want, maxc));
+        p->adj_wpb = kWarpsPerBlock;
         in.fwd_blocks = (long long)p->fwd_chunks * K;
-        in.adj_blocks = (g.nbricks + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        in.adj_blocks = (g.nbricks + p->adj_wpb - 1) / p->adj_wpb;
         if (!(in.dist_min >= kappa)) {
             rc = fail(PAT_ERR_GEOMETRY, "dist_min = %.6g m < kappa = %.6g m (Assumption 1(iii))", in.dist_min, kappa);
             break;
@@ -419,6 +421,8 @@ static size_t ws_f(const pat_plan *p) { return p->tc ? align256(sizeof(float) * 
 static size_t ws_fwd(const pat_plan *p) { return ws_D(p) + ws_f(p); }
 static size_t ws_adj(const pat_plan *p) { return ws_P(p) + ws_f(p); }
 static size_t ws_fwd_dc(const pat_plan *p) { return 2 * ws_D(p); }
+// autotuning: operator workspace, then z [N]
+static size_t ws_tune(const pat_plan *p) { return std::max(ws_fwd(p), ws_adj(p)) + align256(sizeof(float) * p->N); }
 static size_t ws_recon(const pat_plan *p)
 {
     return std::max(ws_fwd(p), ws_adj(p)) + align256(sizeof(float) * (size_t)p->K * p->tm.L) +
@@ -432,6 +436,7 @@ extern "C" size_t pat_workspace_bytes(const pat_plan *p, int32_t op)
     if (op == PAT_OP_ADJOINT) return ws_adj(p);
     if (op == PAT_OP_RECON) return ws_recon(p);
     if (op == PAT_OP_FORWARD_DC) return ws_fwd_dc(p);
+    if (op == PAT_OP_AUTOTUNE) return ws_tune(p);
     return 0;
 }
 
@@ -473,7 +478,7 @@ static pat_status enqueue_adjoint(pat_plan *p, const float *in, int from_v, floa
         from_v = 1;
     }
     CK(launch_adj_conv(in, from_v, p->W, p->nW, p->n_lo, p->tm, mode, p->K, ws, st));
-    CK(launch_adj_geom(p->tx, p->K, p->kind_all, p->tm, p->g, ws, z, st));
+    CK(launch_adj_geom(p->tx, p->K, p->kind_all, p->tm, p->g, ws, z, st, p->adj_wpb));
     return PAT_OK;
 }
 
@@ -567,6 +572,126 @@ extern "C" pat_status pat_forward_dc(pat_plan *p, const float *x, const double *
 // ---------------------------------------------------------------------------
 // projected FISTA (Eq. nnls_tik)
 // ---------------------------------------------------------------------------
+// Workspace of one problem: operator workspace, residual r [K][L], then y,
+// x_old, g, v [N] (v: power iteration).
+struct ReconBufs {
+    void *opws;
+    float *r, *y, *xo, *g, *v;
+};
+
+static ReconBufs recon_bufs(const pat_plan *p, void *ws)
+{
+    char *w = (char *)ws;
+    ReconBufs b;
+    b.opws = w;
+    w += std::max(ws_fwd(p), ws_adj(p));
+    b.r = (float *)w;
+    w += align256(sizeof(float) * (size_t)p->K * p->tm.L);
+    b.y = (float *)w;
+    w += align256(sizeof(float) * (size_t)p->N);
+    b.xo = (float *)w;
+    w += align256(sizeof(float) * (size_t)p->N);
+    b.g = (float *)w;
+    w += align256(sizeof(float) * (size_t)p->N);
+    b.v = (float *)w;
+    return b;
+}
+
+// 1 / (1.05 (|A^T A| + lambda)) by 20 power iterations (synchronises cs)
+static pat_status recon_step(pat_plan *p, const ReconBufs &b, const float *x, float lambda_R, float *step,
+                             cudaStream_t cs)
+{
+    const long long N = p->N;
+    CK(cudaMemcpyAsync(b.v, x, sizeof(float) * N, cudaMemcpyDeviceToDevice, cs));
+    CK(launch_dot(b.v, b.v, N, p->scal, cs));
+    double nv = 0;
+    CK(cudaMemcpyAsync(&nv, p->scal, sizeof(double), cudaMemcpyDeviceToHost, cs));
+    CK(cudaStreamSynchronize(cs));
+    if (!(nv > 0)) {
+        std::vector<float> ones((size_t)N, 1.f);
+        CK(cudaMemcpyAsync(b.v, ones.data(), sizeof(float) * N, cudaMemcpyHostToDevice, cs));
+        CK(cudaStreamSynchronize(cs));
+    }
+    CK(launch_dot(b.v, b.v, N, p->scal, cs));
+    CK(launch_scale(b.v, b.v, N, p->scal, cs));
+    double lam_max = 0;
+    for (int it = 0; it < 20; ++it) {
+        pat_status e = enqueue_forward(p, b.v, b.r, nullptr, b.opws, cs);
+        if (e != PAT_OK) return e;
+        e = enqueue_adjoint(p, b.r, 0, b.g, b.opws, cs);
+        if (e != PAT_OK) return e;
+        CK(launch_dot(b.g, b.v, N, p->scal, cs)); // Rayleigh quotient, |v| = 1
+        CK(launch_dot(b.g, b.g, N, p->scal + 1, cs));
+        double h[2];
+        CK(cudaMemcpyAsync(h, p->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, cs));
+        CK(cudaStreamSynchronize(cs));
+        lam_max = h[0];
+        if (!(h[1] > 0)) break;
+        CK(launch_scale(b.g, b.v, N, p->scal + 1, cs));
+    }
+    const double Lc = lam_max + lambda_R;
+    if (!(Lc > 0)) return fail(PAT_ERR_INVALID_ARG, "pat_recon: operator norm estimate is zero");
+    *step = (float)(1.0 / (1.05 * Lc));
+    return PAT_OK;
+}
+
+// y = x_old = x0, t = 1 (device scalars scal[4], scal[5])
+static pat_status recon_init(pat_plan *p, const ReconBufs &b, const float *x, cudaStream_t cs)
+{
+    static const double t0[2] = {1.0, 0.0};
+    CK(cudaMemcpyAsync(b.y, x, sizeof(float) * p->N, cudaMemcpyDeviceToDevice, cs));
+    CK(cudaMemcpyAsync(b.xo, x, sizeof(float) * p->N, cudaMemcpyDeviceToDevice, cs));
+    CK(cudaMemcpyAsync(p->scal + 4, t0, sizeof(t0), cudaMemcpyHostToDevice, cs));
+    return PAT_OK;
+}
+
+// One FISTA iteration: r = A y - s, g = A^T r, momentum, projected update.
+// The same launches every time (all scalars on the device).
+static pat_status recon_iteration(pat_plan *p, const ReconBufs &b, const float *s, float step, float lambda_R,
+                                  cudaStream_t cs)
+{
+    pat_status e = enqueue_forward(p, b.y, b.r, nullptr, b.opws, cs);
+    if (e != PAT_OK) return e;
+    CK(launch_sub(b.r, s, b.r, (long long)p->K * p->tm.L, cs));
+    e = enqueue_adjoint(p, b.r, 0, b.g, b.opws, cs);
+    if (e != PAT_OK) return e;
+    CK(launch_fista(b.y, b.g, b.xo, p->N, step, lambda_R, p->scal + 4, cs));
+    return PAT_OK;
+}
+
+// Can work on cs be captured into a graph here?  Not on the legacy stream and
+// not while the caller is capturing cs already (the iterations then go into
+// the caller's graph as plain launches).
+static bool capturable(cudaStream_t cs)
+{
+    if (cs == nullptr || cs == cudaStreamLegacy || cs == cudaStreamPerThread) return false;
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(cs, &st) != cudaSuccess) return false;
+    return st == cudaStreamCaptureStatusNone;
+}
+
+// Captures build(cs) once into a graph and launches it n times on cs.
+template <class Build> static pat_status replay(cudaStream_t cs, int n, Build build)
+{
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    pat_status e = build(cs);
+    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    if (e != PAT_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return e;
+    }
+    CK(ce);
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ce);
+    for (int i = 0; i < n && ce == cudaSuccess; ++i) ce = cudaGraphLaunch(exec, cs);
+    cudaGraphExecDestroy(exec); // freed once the launches in flight complete
+    CK(ce);
+    return PAT_OK;
+}
+
 extern "C" pat_status pat_recon(pat_plan *p, const float *s, float *x, int32_t iters, float lambda_R, float step,
                                 void *ws, size_t ws_bytes, void *stream)
 {
@@ -576,66 +701,165 @@ extern "C" pat_status pat_recon(pat_plan *p, const float *s, float *x, int32_t i
     pat_status st = check_ws(p, ws, ws_bytes, ws_recon(p), "pat_recon");
     if (st != PAT_OK) return st;
     cudaStream_t cs = (cudaStream_t)stream;
-    char *w = (char *)ws;
-    void *opws = w;
-    w += std::max(ws_fwd(p), ws_adj(p));
-    float *r = (float *)w;
-    w += align256(sizeof(float) * (size_t)p->K * p->tm.L);
-    const long long N = p->N, M = (long long)p->K * p->tm.L;
-    float *y = (float *)w;
-    w += align256(sizeof(float) * (size_t)N);
-    float *xo = (float *)w;
-    w += align256(sizeof(float) * (size_t)N);
-    float *g = (float *)w;
-    w += align256(sizeof(float) * (size_t)N);
-    float *v = (float *)w;
+    const ReconBufs b = recon_bufs(p, ws);
     if (!(step > 0)) {
-        // power iteration on A^T A + lambda I from x (or ones where x vanishes)
-        CK(cudaMemcpyAsync(v, x, sizeof(float) * N, cudaMemcpyDeviceToDevice, cs));
-        CK(launch_dot(v, v, N, p->scal, cs));
-        double nv = 0;
-        CK(cudaMemcpyAsync(&nv, p->scal, sizeof(double), cudaMemcpyDeviceToHost, cs));
-        CK(cudaStreamSynchronize(cs));
-        if (!(nv > 0)) {
-            std::vector<float> ones((size_t)N, 1.f);
-            CK(cudaMemcpyAsync(v, ones.data(), sizeof(float) * N, cudaMemcpyHostToDevice, cs));
-            CK(cudaStreamSynchronize(cs));
-        }
-        CK(launch_dot(v, v, N, p->scal, cs));
-        CK(launch_scale(v, v, N, p->scal, cs));
-        double lam_max = 0;
-        for (int it = 0; it < 20; ++it) {
-            pat_status e = enqueue_forward(p, v, r, nullptr, opws, cs);
-            if (e != PAT_OK) return e;
-            e = enqueue_adjoint(p, r, 0, g, opws, cs);
-            if (e != PAT_OK) return e;
-            CK(launch_dot(g, v, N, p->scal, cs)); // Rayleigh quotient, |v| = 1
-            CK(launch_dot(g, g, N, p->scal + 1, cs));
-            double h[2];
-            CK(cudaMemcpyAsync(h, p->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, cs));
-            CK(cudaStreamSynchronize(cs));
-            lam_max = h[0];
-            if (!(h[1] > 0)) break;
-            CK(launch_scale(g, v, N, p->scal + 1, cs));
-        }
-        double Lc = lam_max + lambda_R;
-        if (!(Lc > 0)) return fail(PAT_ERR_INVALID_ARG, "pat_recon: operator norm estimate is zero");
-        step = (float)(1.0 / (1.05 * Lc));
+        st = recon_step(p, b, x, lambda_R, &step, cs);
+        if (st != PAT_OK) return st;
     }
-    CK(cudaMemcpyAsync(y, x, sizeof(float) * N, cudaMemcpyDeviceToDevice, cs));
-    CK(cudaMemcpyAsync(xo, x, sizeof(float) * N, cudaMemcpyDeviceToDevice, cs));
-    double t = 1.0;
-    for (int it = 0; it < iters; ++it) {
-        pat_status e = enqueue_forward(p, y, r, nullptr, opws, cs);
-        if (e != PAT_OK) return e;
-        CK(launch_sub(r, s, r, M, cs));
-        e = enqueue_adjoint(p, r, 0, g, opws, cs);
-        if (e != PAT_OK) return e;
-        double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-        CK(launch_fista(y, g, xo, N, step, lambda_R, (float)((t - 1.0) / tn), cs));
-        t = tn;
+    st = recon_init(p, b, x, cs);
+    if (st != PAT_OK) return st;
+    if (iters >= 2 && capturable(cs)) {
+        st = replay(cs, iters, [&](cudaStream_t c) { return recon_iteration(p, b, s, step, lambda_R, c); });
+    } else {
+        for (int it = 0; it < iters && st == PAT_OK; ++it) st = recon_iteration(p, b, s, step, lambda_R, cs);
     }
-    CK(cudaMemcpyAsync(x, xo, sizeof(float) * N, cudaMemcpyDeviceToDevice, cs));
+    if (st != PAT_OK) return st;
+    CK(cudaMemcpyAsync(x, b.xo, sizeof(float) * p->N, cudaMemcpyDeviceToDevice, cs));
+    return PAT_OK;
+}
+
+extern "C" pat_status pat_recon_batch(pat_plan *const *plans, int32_t nprob, const float *const *s, float *const *x,
+                                      int32_t iters, const float *lambda_R, const float *step, void *const *ws,
+                                      const size_t *ws_bytes, void *stream)
+{
+    g_err.clear();
+    if (!plans || !s || !x || !lambda_R || !ws || !ws_bytes || nprob < 1 || iters < 0)
+        return fail(PAT_ERR_INVALID_ARG, "pat_recon_batch: null pointer, nprob < 1 or iters < 0");
+    for (int i = 0; i < nprob; ++i) {
+        if (!plans[i] || !s[i] || !x[i]) return fail(PAT_ERR_INVALID_ARG, "pat_recon_batch: problem %d: null pointer", i);
+        if (!(lambda_R[i] >= 0)) return fail(PAT_ERR_INVALID_ARG, "pat_recon_batch: problem %d: lambda_R < 0", i);
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) return fail(PAT_ERR_INVALID_ARG, "pat_recon_batch: plan of problem %d repeats", i);
+        pat_status st = check_ws(plans[i], ws[i], ws_bytes[i], ws_recon(plans[i]), "pat_recon_batch");
+        if (st != PAT_OK) return st;
+    }
+    cudaStream_t cs = (cudaStream_t)stream;
+    std::vector<ReconBufs> b((size_t)nprob);
+    std::vector<float> stp((size_t)nprob);
+    for (int i = 0; i < nprob; ++i) {
+        b[i] = recon_bufs(plans[i], ws[i]);
+        stp[i] = step ? step[i] : 0.f;
+        if (!(stp[i] > 0)) {
+            pat_status st = recon_step(plans[i], b[i], x[i], lambda_R[i], &stp[i], cs);
+            if (st != PAT_OK) return st;
+        }
+        pat_status st = recon_init(plans[i], b[i], x[i], cs);
+        if (st != PAT_OK) return st;
+    }
+    pat_status st = PAT_OK;
+    if (iters >= 1 && nprob > 1 && capturable(cs)) {
+        // one graph per iteration of all problems: a fork to one stream per
+        // problem and a join, so independent problems overlap on the GPU
+        std::vector<cudaStream_t> sub((size_t)nprob, nullptr);
+        std::vector<cudaEvent_t> ev((size_t)nprob + 1, nullptr);
+        cudaError_t ce = cudaSuccess;
+        for (int i = 0; i < nprob && ce == cudaSuccess; ++i) ce = cudaStreamCreateWithFlags(&sub[i], cudaStreamNonBlocking);
+        for (int i = 0; i <= nprob && ce == cudaSuccess; ++i) ce = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+        if (ce == cudaSuccess) {
+            st = replay(cs, iters, [&](cudaStream_t c) -> pat_status {
+                CK(cudaEventRecord(ev[nprob], c));
+                for (int i = 0; i < nprob; ++i) {
+                    CK(cudaStreamWaitEvent(sub[i], ev[nprob], 0));
+                    pat_status e = recon_iteration(plans[i], b[i], s[i], stp[i], lambda_R[i], sub[i]);
+                    if (e != PAT_OK) return e;
+                    CK(cudaEventRecord(ev[i], sub[i]));
+                    CK(cudaStreamWaitEvent(c, ev[i], 0));
+                }
+                return PAT_OK;
+            });
+        } else {
+            st = fail(PAT_ERR_CUDA, "pat_recon_batch: stream or event creation failed: %s", cudaGetErrorString(ce));
+        }
+        for (auto e : ev)
+            if (e) cudaEventDestroy(e);
+        for (auto q : sub)
+            if (q) cudaStreamDestroy(q);
+    } else {
+        for (int it = 0; it < iters && st == PAT_OK; ++it)
+            for (int i = 0; i < nprob && st == PAT_OK; ++i)
+                st = recon_iteration(plans[i], b[i], s[i], stp[i], lambda_R[i], cs);
+    }
+    if (st != PAT_OK) return st;
+    for (int i = 0; i < nprob; ++i)
+        CK(cudaMemcpyAsync(x[i], b[i].xo, sizeof(float) * plans[i]->N, cudaMemcpyDeviceToDevice, cs));
+    return PAT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuning of the launch shapes
+// ---------------------------------------------------------------------------
+extern "C" pat_status pat_plan_autotune(pat_plan *p, const float *x, void *ws, size_t ws_bytes, void *stream)
+{
+    g_err.clear();
+    if (!p || !x) return fail(PAT_ERR_INVALID_ARG, "pat_plan_autotune: null pointer");
+    pat_status st = check_ws(p, ws, ws_bytes, ws_tune(p), "pat_plan_autotune");
+    if (st != PAT_OK) return st;
+    if (!capturable((cudaStream_t)stream) && stream != nullptr)
+        return fail(PAT_ERR_INVALID_ARG, "pat_plan_autotune: the stream is being captured");
+    cudaStream_t cs = (cudaStream_t)stream;
+    double *D = (double *)ws;
+    float *z = (float *)((char *)ws + std::max(ws_fwd(p), ws_adj(p)));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    auto timed = [&](auto launch) -> float {
+        float best = 3.0e38f;
+        for (int rep = 0; rep < 3; ++rep) { // the first run warms up
+            if (cudaEventRecord(e0, cs) != cudaSuccess || launch() != cudaSuccess ||
+                cudaEventRecord(e1, cs) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+                return -1.f;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) best = std::min(best, ms);
+        }
+        return best;
+    };
+    // forward: CTAs per transducer
+    const long long maxc = std::max(1LL, p->g.nbricks / kWarpsPerBlock);
+    const int c0 = p->fwd_chunks;
+    int best_c = c0;
+    float best_t = 3.0e38f;
+    std::vector<long long> tried;
+    for (int f : {1, 2, 4, 8, 16}) { // c0 / 4 ... 4 c0
+        const long long c = std::max(1LL, std::min(maxc, (long long)c0 * f / 4));
+        if (std::find(tried.begin(), tried.end(), c) != tried.end()) continue;
+        tried.push_back(c);
+        const float t = timed([&] {
+            return launch_fwd_geom(p->tx, p->K, p->kind_all, p->tm, p->g, x, D, (int)c, p->fwd_base, p->fwd_span, cs);
+        });
+        if (t < 0.f) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return fail(PAT_ERR_CUDA, "pat_plan_autotune: forward launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        }
+        if (t < best_t) {
+            best_t = t;
+            best_c = (int)c;
+        }
+    }
+    // adjoint gather: bricks per CTA (the workspace holds finite values from
+    // the forward runs; the timing does not depend on them)
+    int best_w = p->adj_wpb;
+    float best_a = 3.0e38f;
+    CK(cudaMemsetAsync(ws, 0, ws_P(p), cs));
+    for (int wpb : {2, 4, 8}) {
+        const float t = timed([&] { return launch_adj_geom(p->tx, p->K, p->kind_all, p->tm, p->g, ws, z, cs, wpb); });
+        if (t < 0.f) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return fail(PAT_ERR_CUDA, "pat_plan_autotune: adjoint launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        }
+        if (t < best_a) {
+            best_a = t;
+            best_w = wpb;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->fwd_chunks = best_c;
+    p->adj_wpb = best_w;
+    p->info.fwd_blocks = (long long)best_c * p->K;
+    p->info.adj_blocks = (p->g.nbricks + best_w - 1) / best_w;
     return PAT_OK;
 }
 

@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(kThreads, 4) adj_geom_kernel(const TxDev *__re
     gl_fill(glx, glw, threadIdx.x);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long br = (long long)blockIdx.x * kWarpsPerBlock + warp;
+    const long long br = (long long)blockIdx.x * (blockDim.x >> 5) + warp; // one brick per warp
     if (br >= g.nbricks) return;
     int ix, iy, iz;
     const bool ok = brick_voxel(g, br, lane, ix, iy, iz); // ragged bricks: idle lanes stay for the syncs
@@ -760,16 +760,30 @@ __global__ void sub_kernel(const float *__restrict__ a, const float *__restrict_
         o[i] = a[i] - b[i];
 }
 
-// x_new = max(0, y - step (g + lam y)); y = x_new + mom (x_new - x_old); x_old = x_new
+// x_new = max(0, y - step (g + lam y)); y = x_new + mom (x_new - x_old); x_old = x_new.
+// The momentum comes from the device scalars of fista_momentum_kernel, so
+// that one iteration is the same launch sequence every time (graph replay).
 __global__ void fista_kernel(float *__restrict__ y, const float *__restrict__ g, float *__restrict__ xo, long long n,
-                             float step, float lam, float mom)
+                             float step, float lam, const double *__restrict__ tstate)
 {
+    const float mom = (float)tstate[1];
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         float yi = y[i];
         float xn = fmaxf(0.f, yi - step * (g[i] + lam * yi));
         float xold = xo[i];
         xo[i] = xn;
         y[i] = xn + mom * (xn - xold);
+    }
+}
+
+// FISTA step-size sequence on the device: t' = (1 + sqrt(1 + 4 t^2)) / 2,
+// momentum (t - 1) / t'.  tstate[0] = t, tstate[1] = momentum of this step.
+__global__ void fista_momentum_kernel(double *__restrict__ tstate)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const double t = tstate[0], tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        tstate[1] = (t - 1.0) / tn;
+        tstate[0] = tn;
     }
 }
 
@@ -903,19 +917,20 @@ cudaError_t launch_adj_conv(const float *s, int from_v, const float *W, int nW, 
 }
 
 cudaError_t launch_adj_geom(const TxDev *tx, int K, int kind, const TimeDev &tm, const GridDev &g, const void *P,
-                            float *z, cudaStream_t st)
+                            float *z, cudaStream_t st, int wpb)
 {
-    unsigned grid = (unsigned)((g.nbricks + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    wpb = wpb == 4 || wpb == 2 ? wpb : kWarpsPerBlock; // warps (bricks) per CTA
+    const unsigned grid = (unsigned)((g.nbricks + wpb - 1) / wpb), thr = 32u * wpb;
     if (tm.method == PAT_METHOD_POINT) {
-        if (kind == PAT_PLANE) adj_geom_kernel<PAT_METHOD_POINT, PAT_PLANE><<<grid, kThreads, 0, st>>>(tx, K, tm, g, P, z);
+        if (kind == PAT_PLANE) adj_geom_kernel<PAT_METHOD_POINT, PAT_PLANE><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z);
         else if (kind == PAT_CYLINDER)
-            adj_geom_kernel<PAT_METHOD_POINT, PAT_CYLINDER><<<grid, kThreads, 0, st>>>(tx, K, tm, g, P, z);
-        else adj_geom_kernel<PAT_METHOD_POINT, kKindAny><<<grid, kThreads, 0, st>>>(tx, K, tm, g, P, z);
+            adj_geom_kernel<PAT_METHOD_POINT, PAT_CYLINDER><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z);
+        else adj_geom_kernel<PAT_METHOD_POINT, kKindAny><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z);
     } else {
-        if (kind == PAT_PLANE) adj_geom_kernel<PAT_METHOD_SURFACE, PAT_PLANE><<<grid, kThreads, 0, st>>>(tx, K, tm, g, P, z);
+        if (kind == PAT_PLANE) adj_geom_kernel<PAT_METHOD_SURFACE, PAT_PLANE><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z);
         else if (kind == PAT_CYLINDER)
-            adj_geom_kernel<PAT_METHOD_SURFACE, PAT_CYLINDER><<<grid, kThreads, 0, st>>>(tx, K, tm, g, P, z);
-        else adj_geom_kernel<PAT_METHOD_SURFACE, kKindAny><<<grid, kThreads, 0, st>>>(tx, K, tm, g, P, z);
+            adj_geom_kernel<PAT_METHOD_SURFACE, PAT_CYLINDER><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z);
+        else adj_geom_kernel<PAT_METHOD_SURFACE, kKindAny><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z);
     }
     return cudaGetLastError();
 }
@@ -946,10 +961,11 @@ cudaError_t launch_sub(const float *a, const float *b, float *o, long long n, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_fista(float *y, const float *g, float *xo, long long n, float step, float lam, float mom,
+cudaError_t launch_fista(float *y, const float *g, float *xo, long long n, float step, float lam, double *tstate,
                          cudaStream_t st)
 {
-    fista_kernel<<<1216, 256, 0, st>>>(y, g, xo, n, step, lam, mom);
+    fista_momentum_kernel<<<1, 32, 0, st>>>(tstate);
+    fista_kernel<<<1216, 256, 0, st>>>(y, g, xo, n, step, lam, tstate);
     return cudaGetLastError();
 }
 

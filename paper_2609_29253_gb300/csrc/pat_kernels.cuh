@@ -26,8 +26,9 @@ cudaError_t launch_fwd_epilogue(const void *in, int in_stride, const float *W, i
                                 int mode, int K, float *s, float *f_out, cudaStream_t st);
 cudaError_t launch_adj_conv(const float *in, int from_v, const float *W, int nW, int n_lo, const TimeDev &tm, int mode,
                             int K, void *out, cudaStream_t st);
+// wpb: warps (4x4x2 voxel bricks) per CTA, 2, 4 or 8
 cudaError_t launch_adj_geom(const TxDev *tx, int K, int kind, const TimeDev &tm, const GridDev &g, const void *P,
-                            float *z, cudaStream_t st);
+                            float *z, cudaStream_t st, int wpb = kWarpsPerBlock);
 // dc: dh-bar/dc instead of h-bar
 cudaError_t launch_taps(int rbf, int eir, double kappa, double c, const double *e, double ufs, int n_lo, int T,
                         double *taps, cudaStream_t st, bool dc = false);
@@ -38,7 +39,8 @@ cudaError_t launch_fwd_dc_epilogue(const double *Dg, const double *Dd, const flo
                                    int nW, int n_lo, const TimeDev &tm, int K, float *ds, cudaStream_t st);
 cudaError_t launch_combine_taps(const double *taps, int T, int U, float *W, cudaStream_t st);
 cudaError_t launch_sub(const float *a, const float *b, float *o, long long n, cudaStream_t st);
-cudaError_t launch_fista(float *y, const float *g, float *xo, long long n, float step, float lam, float mom,
+// advances the device momentum state tstate = {t, momentum}, then the update
+cudaError_t launch_fista(float *y, const float *g, float *xo, long long n, float step, float lam, double *tstate,
                          cudaStream_t st);
 cudaError_t launch_dot(const float *a, const float *b, long long n, double *out, cudaStream_t st);
 cudaError_t launch_scale(const float *a, float *o, long long n, const double *nrm2, cudaStream_t st);
