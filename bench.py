@@ -58,6 +58,11 @@ def parse():
     p.add_argument("--cpu-sample-voxels", type=int, default=1024)
     p.add_argument("--grid", type=int, default=128,
                    help="voxels per axis over the same 12.8 mm cube (128 = the c2 grid; smaller for profiling)")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the convolution, batched-FISTA and c3 comparisons after the main timing")
+    p.add_argument("--fista-problems", type=int, default=8)
+    p.add_argument("--fista-iters", type=int, default=10)
+    p.add_argument("--c3-positions", type=int, default=128)
     return p.parse_args()
 
 
@@ -189,6 +194,136 @@ def c2w(args, angles, with_x=True):
     return w
 
 
+def cuda_ms(fn, reps=3, warm=1):
+    """Mean device time (ms) of fn() on the current stream, CUDA events."""
+    import torch
+
+    for _ in range(warm):
+        fn()
+    st = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(st)
+    for _ in range(reps):
+        fn()
+    b.record(st)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def rel_l2(a, b):
+    a, b = a.double(), b.double()
+    return float((a - b).norm() / b.norm())
+
+
+def conv_compare(api, plan, w, taps, x, dev):
+    """The temporal convolution of A and of A^T on one batch: FP64-accumulated
+    CUDA-core kernels of the plain plan against the tcgen05 BF16 split
+    Toeplitz kernels of a PAT_FLAG_CONV_TC plan (same f and s)."""
+    tc = api.Plan(w, taps=taps, conv_tc=True, device=dev)
+    f = plan.forward_geometric(x)
+    s_plain = plan.conv_forward(f)
+    s_tc = tc.conv_forward(f)
+    v_plain = plan.conv_adjoint(s_plain)
+    v_tc = tc.conv_adjoint(s_plain)
+    out = {"workload": f"the main batch: K {w.K} rows, U L {w.UL} fine bins -> L {w.L}, {w.T + w.U - 1} taps",
+           "forward_ms": {"fp64_cuda_cores": cuda_ms(lambda: plan.conv_forward(f)),
+                          "tcgen05_bf16x3": cuda_ms(lambda: tc.conv_forward(f))},
+           "adjoint_ms": {"fp64_cuda_cores": cuda_ms(lambda: plan.conv_adjoint(s_plain)),
+                          "tcgen05_bf16x3": cuda_ms(lambda: tc.conv_adjoint(s_plain))},
+           "rel_l2_tc_vs_fp64": {"forward": rel_l2(s_tc, s_plain), "adjoint": rel_l2(v_tc, v_plain)},
+           "step_ms_with_tc": cuda_ms(lambda: (tc.forward(x), tc.adjoint(s_plain)), reps=1)}
+    out["tc_error"] = api._lib.pat_plan_get_info(tc.handle)["tc_error"]
+    return out
+
+
+def fista_compare(api, dev, n_prob, iters):
+    """Batched reconstruction (c4-shaped, reduced sizes): n_prob problems of
+    uneven grids, position counts and lengths, s = A x + 1 % noise.  Time per
+    iteration of all problems: one pat_recon per problem enqueued on the
+    legacy stream (plain FP32 operator, no graph), against pat_recon_batch
+    (one CUDA graph per iteration, a branch per problem) with the plain and
+    with the tensor-core-convolution plans."""
+    import torch
+
+    ws = [W.c4_problem(p, n_range=(24, 40), k_range=(128, 384)) for p in range(n_prob)]
+    plans = [api.Plan(w, device=dev) for w in ws]
+    plans_tc = [api.Plan(w, taps=p.taps, conv_tc=True, device=dev) for w, p in zip(ws, plans)]
+    g = torch.Generator(device=dev).manual_seed(1234)
+    s_list, lam, steps = [], [], []
+    for w, p in zip(ws, plans):
+        s0 = p.forward(torch.from_numpy(w.x).to(dev))
+        s = s0 + 0.01 * s0.abs().max() * torch.randn(s0.shape, device=dev, generator=g)
+        s_list.append(s.contiguous())
+        z = p.adjoint(s.contiguous())
+        lam.append(float(1e-3 * z.abs().max()))
+        v = torch.ones(w.N, device=dev)
+        for _ in range(20):
+            v = p.adjoint(p.forward((v.double() / v.double().norm()).float()))
+        steps.append(float(1.0 / (1.05 * (float(v.double().norm()) + lam[-1]))))
+        if not (math.isfinite(lam[-1]) and math.isfinite(steps[-1])):
+            raise RuntimeError(f"{w.name}: lambda {lam[-1]}, step {steps[-1]}, |s0| {float(s0.abs().max())}, "
+                               f"finite s0 {bool(torch.isfinite(s0).all())}, finite z {bool(torch.isfinite(z).all())}, "
+                               f"finite v {bool(torch.isfinite(v).all())}, |x| {float(np.abs(w.x).max())}")
+    x0 = [torch.zeros(p.N, device=dev) for p in plans]
+
+    def seq():
+        return [p.recon(s, x, iters=iters, lambda_R=l, step=t) for p, s, x, l, t in zip(plans, s_list, x0, lam, steps)]
+
+    side = torch.cuda.Stream(device=dev)
+
+    def batched(ps):
+        with torch.cuda.stream(side):
+            r = api.recon_batch(ps, s_list, x0, iters=iters, lambdas=lam, steps=steps)
+        side.synchronize()
+        return r
+
+    def wall(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) * 1e3 / iters, r
+
+    t_seq, r_seq = wall(seq)
+    t_b, r_b = wall(lambda: batched(plans))
+    t_tc, r_tc = wall(lambda: batched(plans_tc))
+    d_b = max(rel_l2(a, b) for a, b in zip(r_b, r_seq))
+    d_tc = max(rel_l2(a, b) for a, b in zip(r_tc, r_seq))
+    pairs = sum(w.N * w.K for w in ws)
+    return {"workload": "; ".join(w.name for w in ws), "problems": n_prob, "iterations": iters,
+            "pairs_per_iteration": 2 * pairs,
+            "ms_per_iteration": {"plain_fp32_sequential": t_seq, "graph_batched": t_b,
+                                 "graph_batched_tcgen05_conv": t_tc},
+            "speedup_vs_plain": {"graph_batched": t_seq / t_b, "graph_batched_tcgen05_conv": t_seq / t_tc},
+            "max_rel_l2_vs_plain": {"graph_batched": d_b, "graph_batched_tcgen05_conv": d_tc},
+            "timing": "wall clock per iteration over all problems, host to device completion, step sizes fixed"}
+
+
+def c3_line(api, dev, n_pos):
+    """The precision-split system (c3): 256^3 voxels at 0.08 mm, planar 3x3 mm
+    elements on a 40 mm hemisphere, L 2048, tcgen05 BF16 split convolution;
+    one batch of the first n_pos positions."""
+    import torch
+
+    w = W.c3(with_x=False, rotations=1)
+    w = w.with_tx(w.tx[:n_pos])
+    w = w.with_(x=W.blob_phantom(w.n, w.origin, w.pitch, 200, 0))
+    plan = api.Plan(w, conv_tc=True, device=dev)
+    x = torch.from_numpy(w.x).to(dev)
+    s = plan.forward(x)
+    t_f = cuda_ms(lambda: plan.forward(x, out=s), reps=2)
+    z = torch.empty(w.N, device=dev)
+    t_a = cuda_ms(lambda: plan.adjoint(s, out=z), reps=2)
+    pairs = w.N * w.K
+    return {"workload": f"c3: 256^3 @ 0.08 mm, first {w.K} of 5,120 planar 3x3 mm positions, L 2048 @ 40 MHz, "
+                        f"U 11, dl 11, tcgen05 BF16 split convolution",
+            "forward_pairs_per_s": pairs / (t_f * 1e-3), "adjoint_pairs_per_s": pairs / (t_a * 1e-3),
+            "ms": {"forward": t_f, "adjoint": t_a}, "mean_bins_per_pair": plan.info["pair_bins"] / pairs,
+            "tc_error": api._lib.pat_plan_get_info(plan.handle)["tc_error"]}
+
+
 def config(args, w):
     grid = "" if args.grid == 128 else f" [reduced grid {args.grid}^3 for profiling]"
     return {"workload": "c2: 128^3 voxels @ 0.1 mm, 128-element cylindrical array (R 20 mm, 10 mm elevation, "
@@ -314,6 +449,13 @@ def main():
         cpu = {"value": v, "unit": "pairs/s", "cores": cores, "kind": "oracle",
                "sample": f"{nv} seeded voxels x {wcpu.K} positions, A then A^T, FP64 ({dt:.1f} s)"}
 
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras["conv_tcgen05"] = conv_compare(api, plans[args.warmup], c2w(args, angle_sets[args.warmup], with_x=False)
+                                              .with_(x=w0.x), taps, x, dev)
+        extras["fista_batched"] = fista_compare(api, dev, args.fista_problems, args.fista_iters)
+        extras["c3_precision_split"] = c3_line(api, dev, args.c3_positions)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_step / args.steps, "higher_is_better": True,
@@ -326,6 +468,7 @@ def main():
                              "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load"},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 4 * args.steps,
                 "clocks": clk, "wall_s_timed": t_wall}
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

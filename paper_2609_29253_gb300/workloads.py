@@ -346,6 +346,31 @@ def c5(with_x=True, n_angles=128):
                  50e6, 1.0e-6, 4096, 11, 1.5 * pitch, gauss_sine_eir(5e6), x=x)
 
 
+def c4_problem(p, n_range=(48, 160), k_range=(1024, 8192), seed_base=1000):
+    """Problem p of the batched-reconstruction set: a cubic grid of n ~ U{n_range}
+    voxels per axis at 0.1 mm, K ~ U{k_range} positions (even p: planar 3x3 mm
+    elements on a 40 mm Fibonacci hemisphere; odd p: the c2 cylindrical array
+    with round(K / 128) >= 1 rotation angles), L in {1024, 2048} at 40 MHz,
+    and 5-15 vessel-like tubes as x (seed seed_base + p)."""
+    rng = np.random.default_rng(seed_base + p)
+    n = int(rng.integers(n_range[0], n_range[1] + 1))
+    K = int(rng.integers(k_range[0], k_range[1] + 1))
+    L = int(rng.choice([1024, 2048]))
+    pitch = 0.1e-3
+    origin = centred_origin((n, n, n), pitch)
+    if p % 2 == 0:
+        tx = fibonacci_planar(K, 40e-3, 1.5e-3, 1.5e-3, hemisphere=True)
+        t0, kind = 16e-6, "planar"
+    else:
+        a = C2_ARRAY
+        n_ang = max(1, int(round(K / a["n_el"])))
+        tx = rotated_linear_cylinder_array(a["n_el"], a["el_pitch"], a["R"], a["theta_max"], a["Lz"], n_ang)
+        t0, kind = 5e-6, "cylindrical"
+    x = tube_phantom((n, n, n), origin, pitch, int(rng.integers(5, 16)), seed_base + p)
+    return _make(f"c4 problem {p}: {n}^3 @ 0.1 mm, {len(tx)} {kind} positions, L={L} @ 40 MHz", (n, n, n), pitch, tx,
+                 1500.0, 40e6, t0, L, 11, 1.5 * pitch, gauss_sine_eir(5e6), x=x)
+
+
 def small_cylinder(n_vox=12, n_angles=4, n_el=4, seed=0, dl=None, L=None):
     """A reduced c2-like system (same element, fewer voxels and positions) for
     parity tests the oracle finishes in seconds."""

@@ -110,6 +110,26 @@ def test_ragged_grid_and_many_tiles(api, orc):
     _run(api, orc, w2)
 
 
+def test_voxels_on_and_near_the_focal_line(api, orc):
+    """An odd grid centred on the focal line (voxels at rho = 0 and, after the
+    frame rotation by pi, at rho ~ 1e-19 m) seen by the whole 128-element
+    array, whose end elements see the axis voxels under a near-flat level
+    curve (both branch points inside one short piece).  t0 is set off the
+    round value 5 us so that no pair's r_min or r_max falls within 1e-5 of
+    a bin edge: with round numbers (R - rho = 19.8 mm at 5 us) some fall
+    exactly on one, and the oracle (FP64) and the kernel (float-float) then
+    round the tie to different bins, which moves the whole first group of
+    Remark 1."""
+    a = W.C2_ARRAY
+    tx = W.rotated_linear_cylinder_array(a["n_el"], a["el_pitch"], a["R"], a["theta_max"], a["Lz"], 2)
+    w = W.c2(angles=np.array([0.0]), with_x=False).with_tx(tx)
+    n = 7
+    w = w.with_(n=(n, n, n), origin=W.centred_origin((n, n, n), 0.1e-3), t0=5.00037e-6, L=2048)
+    w = w.with_(x=W.uniform_phantom(n ** 3, 9))
+    plan, s, s_ref = _run(api, orc, w, check_stages=False)
+    assert np.isfinite(s).all()
+
+
 def test_single_voxel_and_single_transducer(api, orc):
     w = W.c1().with_(n=(1, 1, 1), origin=np.array([0.05e-3, -0.02e-3, 0.01e-3]), x=np.array([0.7], dtype=np.float32))
     w = w.with_tx(w.tx[:1])
