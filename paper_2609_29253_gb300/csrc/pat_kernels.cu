@@ -233,7 +233,7 @@ struct FwdPointSink {
 // scan); span: window length shared by all k.  Dg: [K][UL + 1] doubles, zeroed
 // by the launcher; each CTA adds its window into row k.
 template <int METHOD, int KIND>
-__global__ void __launch_bounds__(kThreads, 4) fwd_geom_kernel(const TxDev *__restrict__ tx, TimeDev tm, GridDev g,
+__global__ void __launch_bounds__(kThreads, 3) fwd_geom_kernel(const TxDev *__restrict__ tx, TimeDev tm, GridDev g,
                                                             const float *__restrict__ x, double *__restrict__ Dg,
                                                             int bricks_per_cta, const int *__restrict__ base,
                                                             int span)
@@ -567,7 +567,7 @@ struct AdjPointSink {
 };
 
 template <int METHOD, int KIND>
-__global__ void __launch_bounds__(kThreads, 4) adj_geom_kernel(const TxDev *__restrict__ tx, int K, TimeDev tm,
+__global__ void __launch_bounds__(kThreads, 3) adj_geom_kernel(const TxDev *__restrict__ tx, int K, TimeDev tm,
                                                             GridDev g, const void *__restrict__ Pv,
                                                             float *__restrict__ z)
 {
