@@ -37,11 +37,16 @@ from paper_2609_29253_gb300 import workloads as W  # noqa: E402
 
 METRIC = "voxel-transducer pairs/s for A and A^T (closed form)"
 N_ANGLES = 180
-# FP32 operations of one quadrant-edge area evaluation of the cylinder path
-# (6-node Gauss-Legendre along v, clamps and branch-point tests; sqrt, asin and
-# reciprocals counted as one operation each), see the roofline section of the
-# design notes.
-FLOPS_PER_QUAD_EVAL = 175
+# FP32 floating-point operations of one quadrant-edge area evaluation of the
+# cylinder path: 2 per FFMA, 1 per FADD / FMUL, 4 per FFMA2, 2 per FADD2 /
+# FMUL2 (MUFU operations not counted), from the instruction counters of one
+# adj_geom_kernel launch on the c2 geometry (64^3 grid, 128 positions,
+# 1.450e9 evaluations): 169.7 (170 for the forward kernel).
+FLOPS_PER_QUAD_EVAL = 170
+# DRAM read + write bytes of one adj_geom_kernel launch of the default
+# workload (128^3 x 512 positions), one-pass ncu capture of this kernel
+# version (29.06 MB read + 12.41 MB written).
+ADJ_TRAFFIC_BYTES = 41.47e6
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -464,7 +469,9 @@ def main():
                 "forward_pairs_per_s": w0.N * K / mean_fwd, "adjoint_pairs_per_s": w0.N * K / mean_adj,
                 "area_evals_per_s": ae / mean_adj, "mean_bins_per_pair": plans[args.warmup].info["pair_bins"] / (w0.N * K),
                 "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                             "traffic": None, "kernel": "adj_geom_kernel",
+                             "traffic": ADJ_TRAFFIC_BYTES if (args.grid == 128 and args.batch_angles == 4) else None,
+                             "kernel": "adj_geom_kernel", "flops_per_unit": FLOPS_PER_QUAD_EVAL,
+                             "units_per_launch": qe, "unit_name": "quadrant-edge area evaluation",
                              "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load"},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 4 * args.steps,
                 "clocks": clk, "wall_s_timed": t_wall}
