@@ -59,6 +59,8 @@ def lib():
                 getattr(L, nm).argtypes = [C.c_double, C.c_double]
             L.oracle_pair_bin_areas.restype = C.c_int64
             L.oracle_pair_bin_areas.argtypes = [_D, _D, _D, _I32, C.POINTER(C.c_int64), _D, C.c_int64]
+            L.oracle_pair_bin_areas_m.restype = C.c_int64
+            L.oracle_pair_bin_areas_m.argtypes = [_D, _D, _D, _I32, C.c_int, C.POINTER(C.c_int64), _D, C.c_int64]
             L.oracle_pair_range.restype = C.c_int
             L.oracle_pair_range.argtypes = [_D, _D, _D]
             geo = [_I32, _D, C.c_double, _D, C.c_int, _D, _I32, C.c_int, C.c_int, C.c_int]
@@ -186,19 +188,23 @@ def h_value(rbf_kind, kappa, eir_kind, eir_par, c, t, panels=3):
                                 np.ascontiguousarray(eir_par, dtype=np.float64), float(c), int(panels), float(t))
 
 
-def pair_bin_areas(tx_row, xi, w):
-    """(b_min, areas per fine bin) of one voxel-transducer pair."""
+METHOD_SURFACE, METHOD_POINT, METHOD_TRAPEZOID = 0, 1, 2
+
+
+def pair_bin_areas(tx_row, xi, w, method=METHOD_SURFACE):
+    """(b_min, areas per fine bin) of one voxel-transducer pair; method
+    METHOD_TRAPEZOID takes the trapezoidal arc integral for a cylinder."""
     tp, ip = time_args(w)
     tx_row = np.ascontiguousarray(tx_row, dtype=np.float64)
     xi = np.ascontiguousarray(xi, dtype=np.float64)
     cap = 1 << 16
     out = np.zeros(cap)
     bmin = C.c_int64(0)
-    nb = lib().oracle_pair_bin_areas(tx_row, xi, tp, ip, C.byref(bmin), out, cap)
+    nb = lib().oracle_pair_bin_areas_m(tx_row, xi, tp, ip, int(method), C.byref(bmin), out, cap)
     if nb < 0:
         cap = -nb
         out = np.zeros(cap)
-        nb = lib().oracle_pair_bin_areas(tx_row, xi, tp, ip, C.byref(bmin), out, cap)
+        nb = lib().oracle_pair_bin_areas_m(tx_row, xi, tp, ip, int(method), C.byref(bmin), out, cap)
     return int(bmin.value), out[:nb].copy()
 
 

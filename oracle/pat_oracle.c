@@ -22,6 +22,9 @@
  *     f_i[l] = 2 pi c, focal-line cylinder formula;
  *   - system-kernel taps against exact rational integration (box EIR);
  *   - the discrete convolution identity of the sampling operator (App. D);
+ *   - the trapezoidal arc integral (Eq. trapezoid_Il): exact on the focal
+ *     line (flat level curves), exact group totals, convergence to the exact
+ *     areas as the strip narrows, its own dot-product test;
  *   - the whole chain against the continuous model (Prop. 1 + Eq. 3,4) at
  *     growing U (Prop. 3), the point method against the surface method at
  *     growing Q (Prop. 2), translation/rotation invariance and the
@@ -39,6 +42,7 @@
 #define OR_CYLINDER 1
 #define OR_METHOD_SURFACE 0
 #define OR_METHOD_POINT 1
+#define OR_METHOD_TRAPEZOID 2 /* surface method, Eq. (trapezoid_Il) for the cylinder arc integral */
 
 /* Transducer descriptor: 16 doubles
  *   [0] kind, [1..3] c0, [4..6] e1, [7..9] e2,
@@ -317,12 +321,24 @@ static double arc_integral(const opair *p, double alpha, double beta, double r)
     return 2.0 * sqrt(q) * (ellip_e_any(0.5 * beta, nu) - ellip_e_any(0.5 * alpha, nu));
 }
 
+/* Trapezoidal approximation of I_l (Eq. trapezoid_Il): the level curve
+ * between (alpha, Psi(alpha)) and (beta, Psi(beta)) replaced by its chord,
+ * Psi(u, r) = sqrt(r^2 - psi(u)) the height at angle u.  Used for the
+ * cylinder only; a plane keeps its closed form. */
+static double arc_integral_trapezoid(const opair *p, double alpha, double beta, double r)
+{
+    if (!(beta > alpha)) return 0.0;
+    if (p->kind == OR_PLANE) return arc_integral(p, alpha, beta, r);
+    double ha = r * r - psi_of(p, alpha), hb = r * r - psi_of(p, beta);
+    return 0.5 * (beta - alpha) * (sqrt(ha > 0.0 ? ha : 0.0) + sqrt(hb > 0.0 ? hb : 0.0));
+}
+
 /* Group areas of one pair (Alg. 4 with the coarser area grid of Remark 1).
  * Bins [b_min, b_max] from Eq. (rmin_rmax); group j covers the fine bins
  * [b_min + j dl, min(b_min + (j+1) dl, b_max + 1)).  Returns the number of
- * groups written into areas[] (grown on demand). */
+ * groups written into areas[] (grown on demand).  trap: the trapezoidal I_l. */
 static int pair_group_areas(const opair *p, const otime *tm, int64_t *bmin_out, int64_t *bmax_out,
-                            double **areas, int *cap)
+                            double **areas, int *cap, int trap)
 {
     const double ufs = (double)tm->U * tm->fs;
     int64_t bmin = (int64_t)floor((p->rmin / tm->c - tm->t0) * ufs);
@@ -354,7 +370,7 @@ static int pair_group_areas(const opair *p, const otime *tm, int64_t *bmin_out, 
             const oquad *q = &p->q[i];
             double a = phi_hat(p, q, q->vmax, r); /* Eq. (alphabeta) */
             double bb = phi_hat(p, q, q->vmin, r);
-            double I = arc_integral(p, a, bb, r);
+            double I = trap ? arc_integral_trapezoid(p, a, bb, r) : arc_integral(p, a, bb, r);
             /* Eq. (area_D_l_xi) and Eq. (swept_u) */
             area += p->J0 * ((a - al[i]) * q->vmax + I - Il[i] - (bb - be[i]) * q->vmin);
             al[i] = a;
@@ -378,9 +394,10 @@ static void voxel_pos(const int *n, const double *origin, double pitch, int64_t 
 
 /* Exported: the pair's bin range and per-fine-bin areas |M_i^l| (each group
  * area split evenly over its fine bins, Remark 1).  out_area has room for
- * cap entries; returns the number of fine bins or -needed when too small. */
-int64_t oracle_pair_bin_areas(const double *tx, const double *x, const double *tp, const int *ip,
-                              int64_t *b_min, double *out_area, int64_t cap)
+ * cap entries; returns the number of fine bins or -needed when too small.
+ * method: OR_METHOD_SURFACE, or OR_METHOD_TRAPEZOID for Eq. (trapezoid_Il). */
+int64_t oracle_pair_bin_areas_m(const double *tx, const double *x, const double *tp, const int *ip, int method,
+                                int64_t *b_min, double *out_area, int64_t cap)
 {
     otime tm = mk_time(tp, ip);
     opair p;
@@ -388,7 +405,7 @@ int64_t oracle_pair_bin_areas(const double *tx, const double *x, const double *t
     double *areas = NULL;
     int acap = 0;
     int64_t bmin, bmax;
-    int ng = pair_group_areas(&p, &tm, &bmin, &bmax, &areas, &acap);
+    int ng = pair_group_areas(&p, &tm, &bmin, &bmax, &areas, &acap, method == OR_METHOD_TRAPEZOID);
     int64_t nb = bmax - bmin + 1;
     *b_min = bmin;
     if (nb > cap) {
@@ -402,6 +419,12 @@ int64_t oracle_pair_bin_areas(const double *tx, const double *x, const double *t
     }
     free(areas);
     return nb < 0 ? 0 : nb;
+}
+
+int64_t oracle_pair_bin_areas(const double *tx, const double *x, const double *tp, const int *ip,
+                              int64_t *b_min, double *out_area, int64_t cap)
+{
+    return oracle_pair_bin_areas_m(tx, x, tp, ip, OR_METHOD_SURFACE, b_min, out_area, cap);
 }
 
 /* Exported: r_min, r_max of Eq. (rmin_rmax) and the quadrant count. */
@@ -489,7 +512,7 @@ int64_t oracle_geometric_forward(const int *n, const double *origin, double pitc
                     opair p;
                     pair_setup(t, xi, &p);
                     int64_t bmin, bmax;
-                    int ng = pair_group_areas(&p, &tm, &bmin, &bmax, &areas, &acap);
+                    int ng = pair_group_areas(&p, &tm, &bmin, &bmax, &areas, &acap, method == OR_METHOD_TRAPEZOID);
                     for (int j = 0; j < ng; ++j) {
                         int64_t e0 = bmin + (int64_t)j * tm.dl, e1 = e0 + tm.dl;
                         if (e1 > bmax + 1) e1 = bmax + 1;
@@ -557,7 +580,7 @@ int64_t oracle_geometric_adjoint(const int *n, const double *origin, double pitc
                     opair p;
                     pair_setup(t, xi, &p);
                     int64_t bmin, bmax;
-                    int ng = pair_group_areas(&p, &tm, &bmin, &bmax, &areas, &acap);
+                    int ng = pair_group_areas(&p, &tm, &bmin, &bmax, &areas, &acap, method == OR_METHOD_TRAPEZOID);
                     for (int j = 0; j < ng; ++j) {
                         int64_t e0 = bmin + (int64_t)j * tm.dl, e1 = e0 + tm.dl;
                         if (e1 > bmax + 1) e1 = bmax + 1;
