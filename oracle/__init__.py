@@ -233,3 +233,62 @@ def ellip_f(phi, m):
 
 def ellip_e_any(theta, nu):
     return lib().oracle_ellip_e_any(theta, nu)
+
+
+# --------------------------------------------------------------------------
+# Piecewise-Planes (Sec. 4.3): a cylindrical element replaced by n_planes
+# planes tangent to it at the centres of equal angular sectors.
+# --------------------------------------------------------------------------
+def piecewise_planes(tx_row, n_planes):
+    """Descriptor rows (16 doubles, plane layout) of the n_planes tangent
+    planes of one cylindrical element: sector j of width 2 theta_max /
+    n_planes has central angle theta_j; its plane touches the cylinder along
+    the generator at theta_j, with half-width R dtheta / 2 across the
+    generator and half-height Lz along the axis e1.  A planar row is
+    returned unchanged (one plane)."""
+    row = np.asarray(tx_row, dtype=np.float64)
+    if int(row[0]) != 1:
+        return row[None, :].copy()
+    c0, e1, e2 = row[1:4], row[4:7], row[7:10]
+    R, th, Lz = float(row[12]), float(row[13]), float(row[14])
+    n = np.cross(e1, e2)
+    dth = 2.0 * th / n_planes
+    out = np.zeros((n_planes, row.size))
+    for j in range(n_planes):
+        tj = -th + (j + 0.5) * dth
+        radial = np.cos(tj) * e2 + np.sin(tj) * n      # from the focal line to the surface
+        tangent = -np.sin(tj) * e2 + np.cos(tj) * n    # along the arc
+        out[j, 0] = 0.0
+        out[j, 1:4] = c0 + R * radial
+        out[j, 4:7] = tangent
+        out[j, 7:10] = e1
+        out[j, 10] = 0.5 * R * dth
+        out[j, 11] = Lz
+    return out
+
+
+def piecewise_planes_forward(w, taps, x, n_planes, vox_idx=None):
+    """s = A x with every cylindrical element replaced by its tangent planes:
+    the planes' signals summed per element (the geometric coefficients add,
+    and the convolution is linear)."""
+    rows, owner = [], []
+    for k, row in enumerate(w.tx):
+        f = piecewise_planes(row, n_planes)
+        rows.append(f)
+        owner += [k] * len(f)
+    wp = w.with_tx(np.concatenate(rows))
+    sp, d = forward(wp, taps, x, vox_idx)
+    s = np.zeros((w.tx.shape[0], w.L))
+    np.add.at(s, np.asarray(owner), sp)
+    return s, d
+
+
+def piecewise_planes_adjoint(w, taps, s, n_planes, vox_idx=None):
+    """The transpose: each element's signal replicated to its planes."""
+    rows, owner = [], []
+    for k, row in enumerate(w.tx):
+        f = piecewise_planes(row, n_planes)
+        rows.append(f)
+        owner += [k] * len(f)
+    wp = w.with_tx(np.concatenate(rows))
+    return adjoint(wp, taps, np.asarray(s)[np.asarray(owner)], vox_idx)
