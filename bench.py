@@ -68,6 +68,7 @@ def parse():
     p.add_argument("--fista-problems", type=int, default=8)
     p.add_argument("--fista-iters", type=int, default=10)
     p.add_argument("--c3-positions", type=int, default=128)
+    p.add_argument("--c5-positions", type=int, default=16)
     return p.parse_args()
 
 
@@ -329,6 +330,37 @@ def c3_line(api, dev, n_pos):
             "tc_error": api._lib.pat_plan_get_info(plan.handle)["tc_error"]}
 
 
+def c5_line(api, dev, n_pos):
+    """The full-scale system (c5): 512^3 voxels at 0.05 mm (134M), the c2
+    array rotated over 128 angles, L 4096 at 50 MHz; the first n_pos
+    positions of one angle, closed form (surface method) against the point
+    method with 16 x 16 points per element (Alg. 2) on a quarter of them."""
+    import torch
+
+    w = W.c5(with_x=False, n_angles=128)
+    w = w.with_tx(w.tx[:n_pos])
+    w = w.with_(x=W.blob_phantom(w.n, w.origin, w.pitch, 200, 0))
+    x = torch.from_numpy(w.x).to(dev)
+    plan = api.Plan(w, device=dev)
+    s = plan.forward(x)
+    t_f = cuda_ms(lambda: plan.forward(x, out=s), reps=1)
+    z = torch.empty(w.N, device=dev)
+    t_a = cuda_ms(lambda: plan.adjoint(s, out=z), reps=1)
+    n_pt = max(1, n_pos // 4)
+    wp = w.with_tx(w.tx[:n_pt]).with_(method=W.METHOD_POINT, q1=16, q2=16)
+    pplan = api.Plan(wp, taps=plan.taps, device=dev)
+    sp = pplan.forward(x)
+    t_pf = cuda_ms(lambda: pplan.forward(x, out=sp), reps=1)
+    pairs = w.N * w.K
+    return {"workload": f"c5: 512^3 @ 0.05 mm, first {w.K} of 16,384 cylindrical positions, L 4096 @ 50 MHz, U 11, "
+                        f"dl 11; point method 16 x 16 on the first {n_pt}",
+            "closed_form": {"forward_pairs_per_s": pairs / (t_f * 1e-3), "adjoint_pairs_per_s": pairs / (t_a * 1e-3),
+                            "ms": {"forward": t_f, "adjoint": t_a}},
+            "point_16x16": {"forward_pairs_per_s": w.N * n_pt / (t_pf * 1e-3), "ms": {"forward": t_pf},
+                            "point_evaluations_per_s": w.N * n_pt * 256 / (t_pf * 1e-3)},
+            "mean_bins_per_pair": plan.info["pair_bins"] / pairs}
+
+
 def config(args, w):
     grid = "" if args.grid == 128 else f" [reduced grid {args.grid}^3 for profiling]"
     return {"workload": "c2: 128^3 voxels @ 0.1 mm, 128-element cylindrical array (R 20 mm, 10 mm elevation, "
@@ -460,6 +492,8 @@ def main():
                                               .with_(x=w0.x), taps, x, dev)
         extras["fista_batched"] = fista_compare(api, dev, args.fista_problems, args.fista_iters)
         extras["c3_precision_split"] = c3_line(api, dev, args.c3_positions)
+        if args.c5_positions > 0:
+            extras["c5_full_scale_subset"] = c5_line(api, dev, args.c5_positions)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,

@@ -45,7 +45,11 @@ typedef enum pat_status {
 } pat_status;
 
 enum { PAT_PLANE = 0, PAT_CYLINDER = 1 };
-enum { PAT_METHOD_SURFACE = 0, PAT_METHOD_POINT = 1 };
+/* PAT_METHOD_TRAPEZOID: the surface method with the paper's trapezoidal
+ * approximation of the cylinder's arc integral (Eq. trapezoid_Il: the level
+ * curve between its two ends replaced by its chord); planes keep their
+ * closed form.  An approximation of PAT_METHOD_SURFACE, cheaper per area. */
+enum { PAT_METHOD_SURFACE = 0, PAT_METHOD_POINT = 1, PAT_METHOD_TRAPEZOID = 2 };
 enum { PAT_RBF_BUMP = 0, PAT_RBF_CONE = 1, PAT_RBF_WENDLAND = 2 };
 enum { PAT_EIR_GAUSS_SINE = 0, PAT_EIR_BOX = 1 };
 /* Plan flags (pat_params.flags, OR-ed):
@@ -57,8 +61,15 @@ enum { PAT_EIR_GAUSS_SINE = 0, PAT_EIR_BOX = 1 };
  *                        (hi + lo), hi*hi + hi*lo + lo*hi accumulated in FP32.
  *                        Areas and accumulation of f stay FP32 / FP64; the
  *                        convolution then carries about 16 significant bits
- *                        per product instead of FP64 accumulation. */
-enum { PAT_FLAG_ALLOW_CLIP = 1, PAT_FLAG_CONV_TC = 2 };
+ *                        per product instead of FP64 accumulation;
+ *   PAT_FLAG_PIECEWISE_PLANES  the paper's Piecewise-Planes approximation
+ *                        (Sec. 4.3): every cylindrical element is replaced by
+ *                        np_planes planes tangent at the centres of equal
+ *                        angular sectors (half-width R dtheta / 2, half-height
+ *                        Lz), whose geometric signals add into the element's
+ *                        row (Eq. plane_decomp_u); planar elements are kept.
+ *                        pat_plan_info counts pairs and windows per plane. */
+enum { PAT_FLAG_ALLOW_CLIP = 1, PAT_FLAG_CONV_TC = 2, PAT_FLAG_PIECEWISE_PLANES = 4 };
 enum { PAT_OP_FORWARD = 1, PAT_OP_ADJOINT = 2, PAT_OP_RECON = 3, PAT_OP_FORWARD_DC = 4, PAT_OP_AUTOTUNE = 5 };
 
 /* Uniform voxel grid (Sec. 2.4): centres origin + pitch * (ix, iy, iz). */
@@ -97,7 +108,8 @@ typedef struct pat_params {
     double c;  /* speed of sound, > 0 */
     double fs; /* sampling frequency, > 0 */
     double t0; /* recording origin, >= 0 */
-    int32_t L, U, dl, method, q1, q2, flags, reserved;
+    int32_t L, U, dl, method, q1, q2, flags;
+    int32_t np_planes; /* PAT_FLAG_PIECEWISE_PLANES: planes per cylindrical element, 1..4096 (else ignored) */
 } pat_params;
 
 /* Radial function and electrical impulse response that define the system

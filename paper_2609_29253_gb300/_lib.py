@@ -20,6 +20,7 @@ PAT_ERR_WORKSPACE = 4
 PAT_OP_FORWARD, PAT_OP_ADJOINT, PAT_OP_RECON, PAT_OP_FORWARD_DC, PAT_OP_AUTOTUNE = 1, 2, 3, 4, 5
 PAT_FLAG_ALLOW_CLIP = 1
 PAT_FLAG_CONV_TC = 2
+PAT_FLAG_PIECEWISE_PLANES = 4
 _STATUS = {0: "PAT_OK", 1: "PAT_ERR_INVALID_ARG", 2: "PAT_ERR_GEOMETRY", 3: "PAT_ERR_WINDOW",
            4: "PAT_ERR_WORKSPACE", 5: "PAT_ERR_CUDA", 6: "PAT_ERR_UNSUPPORTED"}
 
@@ -37,7 +38,7 @@ class pat_grid(C.Structure):
 class pat_params(C.Structure):
     _fields_ = [("c", C.c_double), ("fs", C.c_double), ("t0", C.c_double), ("L", C.c_int32), ("U", C.c_int32),
                 ("dl", C.c_int32), ("method", C.c_int32), ("q1", C.c_int32), ("q2", C.c_int32),
-                ("flags", C.c_int32), ("reserved", C.c_int32)]
+                ("flags", C.c_int32), ("np_planes", C.c_int32)]
 
 
 class pat_system(C.Structure):
@@ -151,11 +152,11 @@ def pat_forward_dc(plan, x, dtaps, ds, ws, stream=None):
 
 
 def pat_plan_create(n, origin, pitch, tx, c, fs, t0, L, U, dl, method, q1, q2, flags, kappa, taps, n_lo,
-                    stream=None):
+                    stream=None, np_planes=0):
     grid = pat_grid((C.c_int32 * 3)(*[int(v) for v in n]), 0, (C.c_double * 3)(*[float(v) for v in origin]),
                     float(pitch))
     par = pat_params(float(c), float(fs), float(t0), int(L), int(U), int(dl), int(method), int(q1), int(q2),
-                     int(flags), 0)
+                     int(flags), int(np_planes))
     tx = np.ascontiguousarray(tx, dtype=np.float64)
     taps = np.ascontiguousarray(taps, dtype=np.float64)
     out = C.c_void_p()

@@ -34,16 +34,18 @@ class Plan:
     and one time axis; see pat_plan_create in include/pat.h."""
 
     def __init__(self, w: Workload, taps: np.ndarray | None = None, allow_clip: bool = False, conv_tc: bool = False,
-                 device=None):
+                 piecewise_planes: int = 0, device=None):
         self.w = w
         self.device = torch.device(device or "cuda")
         with torch.cuda.device(self.device):
             if taps is None:
                 taps = system_taps(w, self.device)
             self.taps = np.ascontiguousarray(taps, dtype=np.float64)
-            flags = (_lib.PAT_FLAG_ALLOW_CLIP if allow_clip else 0) | (_lib.PAT_FLAG_CONV_TC if conv_tc else 0)
+            flags = (_lib.PAT_FLAG_ALLOW_CLIP if allow_clip else 0) | (_lib.PAT_FLAG_CONV_TC if conv_tc else 0) | \
+                    (_lib.PAT_FLAG_PIECEWISE_PLANES if piecewise_planes > 0 else 0)
             self.handle = _lib.pat_plan_create(w.n, w.origin, w.pitch, w.tx, w.c, w.fs, w.t0, w.L, w.U, w.dl,
-                                               w.method, w.q1, w.q2, flags, w.kappa, self.taps, w.n_lo)
+                                               w.method, w.q1, w.q2, flags, w.kappa, self.taps, w.n_lo,
+                                               np_planes=piecewise_planes)
         self.info = _lib.pat_plan_get_info(self.handle)
         self._ws = {}
         self.N, self.K, self.L, self.UL = w.N, w.K, w.L, w.UL

@@ -28,6 +28,8 @@ struct pat_plan {
     double *taps;
     float *W;
     int T, nW, n_lo;
+    int Kf;         // elements after the piecewise-planes expansion (== K without it)
+    int *rows;      // per element: its signal row
     int fwd_chunks; // CTAs per transducer of the forward geometric kernel
     int adj_wpb;    // warps (voxel bricks) per CTA of the adjoint gather
     int *fwd_base;  // per transducer: first fine-bin edge of its window
@@ -120,14 +122,16 @@ static pat_status validate(const pat_grid *grid, const pat_transducer *tx, int K
     if (p->L < 1 || p->U < 1 || p->dl < 1 || p->dl > p->U)
         return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: need L >= 1, U >= 1, 1 <= dl <= U");
     if ((long long)p->L * p->U >= (1LL << 30)) return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: U L too large");
-    if (p->method != PAT_METHOD_SURFACE && p->method != PAT_METHOD_POINT)
+    if (p->method != PAT_METHOD_SURFACE && p->method != PAT_METHOD_POINT && p->method != PAT_METHOD_TRAPEZOID)
         return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: unknown method %d", p->method);
     if (p->method == PAT_METHOD_POINT && (p->q1 < 1 || p->q2 < 1))
         return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: point method needs q1, q2 >= 1");
     if (!(kappa > 0)) return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: kappa must be > 0");
     if (n_taps < 1) return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: n_taps must be >= 1");
-    if (p->flags & ~(PAT_FLAG_ALLOW_CLIP | PAT_FLAG_CONV_TC))
+    if (p->flags & ~(PAT_FLAG_ALLOW_CLIP | PAT_FLAG_CONV_TC | PAT_FLAG_PIECEWISE_PLANES))
         return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: unknown flags 0x%x", p->flags);
+    if ((p->flags & PAT_FLAG_PIECEWISE_PLANES) && (p->np_planes < 1 || p->np_planes > 4096))
+        return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: np_planes must be in [1, 4096]");
     for (int k = 0; k < K; ++k) {
         const pat_transducer &t = tx[k];
         int kind = (int)t.kind;
@@ -146,6 +150,43 @@ static pat_status validate(const pat_grid *grid, const pat_transducer *tx, int K
     return PAT_OK;
 }
 
+// Piecewise-Planes (Sec. 4.3): the aperture [-theta_max, theta_max] cut into
+// np equal sectors, sector j replaced by the plane tangent to the cylinder
+// along the generator at its central angle theta_j, half-width R dtheta / 2
+// across the generator and half-height Lz along the axis.  Planar elements
+// pass through.  rows[j] = the element each plane belongs to.
+static void expand_planes(const pat_transducer *tx, int K, int np, std::vector<pat_transducer> &out,
+                          std::vector<int> &rows)
+{
+    for (int k = 0; k < K; ++k) {
+        const pat_transducer &t = tx[k];
+        if ((int)t.kind != PAT_CYLINDER) {
+            out.push_back(t);
+            rows.push_back(k);
+            continue;
+        }
+        const double n[3] = {t.e1[1] * t.e2[2] - t.e1[2] * t.e2[1], t.e1[2] * t.e2[0] - t.e1[0] * t.e2[2],
+                             t.e1[0] * t.e2[1] - t.e1[1] * t.e2[0]};
+        const double dth = 2.0 * t.theta_max / np;
+        for (int j = 0; j < np; ++j) {
+            const double th = -t.theta_max + (j + 0.5) * dth, c = cos(th), sn = sin(th);
+            pat_transducer f;
+            memset(&f, 0, sizeof(f));
+            f.kind = PAT_PLANE;
+            for (int d = 0; d < 3; ++d) {
+                const double radial = c * t.e2[d] + sn * n[d];
+                f.c0[d] = t.c0[d] + t.R * radial;
+                f.e1[d] = -sn * t.e2[d] + c * n[d]; // along the arc
+                f.e2[d] = t.e1[d];                  // along the axis
+            }
+            f.L1 = 0.5 * t.R * dth;
+            f.L2 = t.Lz;
+            out.push_back(f);
+            rows.push_back(k);
+        }
+    }
+}
+
 extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, const pat_transducer *tx, int32_t K,
                                       const pat_params *params, double kappa, const double *taps_host,
                                       int32_t n_taps, int32_t n_lo, void *stream)
@@ -155,18 +196,29 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
     *out = nullptr;
     pat_status st = validate(grid, tx, K, params, kappa, taps_host, n_taps);
     if (st != PAT_OK) return st;
+    std::vector<pat_transducer> facets;
+    std::vector<int> rows_h;
+    if (params->flags & PAT_FLAG_PIECEWISE_PLANES) {
+        expand_planes(tx, K, params->np_planes, facets, rows_h);
+    } else {
+        facets.assign(tx, tx + K);
+        for (int k = 0; k < K; ++k) rows_h.push_back(k);
+    }
+    const int Kf = (int)facets.size();
+    const pat_transducer *fx = facets.data();
     cudaStream_t s = (cudaStream_t)stream;
     pat_plan *p = new pat_plan();
     memset(p, 0, sizeof(*p));
     CK(cudaGetDevice(&p->device));
     p->K = K;
+    p->Kf = Kf;
     p->grid = *grid;
     p->params = *params;
     p->kappa = kappa;
     p->N = (long long)grid->n[0] * grid->n[1] * grid->n[2];
-    p->kind_all = (int)tx[0].kind;
-    for (int k = 1; k < K; ++k)
-        if ((int)tx[k].kind != p->kind_all) p->kind_all = kKindAny;
+    p->kind_all = (int)fx[0].kind;
+    for (int k = 1; k < Kf; ++k)
+        if ((int)fx[k].kind != p->kind_all) p->kind_all = kKindAny;
     GridDev &g = p->g;
     g.nx = grid->n[0];
     g.ny = grid->n[1];
@@ -228,11 +280,12 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
         cudaFree(raw);
         cudaFree(dorig);
     };
-    if (cudaMalloc(&raw, sizeof(double) * 16 * (size_t)K) != cudaSuccess ||
-        cudaMalloc(&p->tx, sizeof(TxDev) * (size_t)K) != cudaSuccess ||
+    if (cudaMalloc(&raw, sizeof(double) * 16 * (size_t)Kf) != cudaSuccess ||
+        cudaMalloc(&p->tx, sizeof(TxDev) * (size_t)Kf) != cudaSuccess ||
+        cudaMalloc(&p->rows, sizeof(int) * (size_t)Kf) != cudaSuccess ||
         cudaMalloc(&p->taps, sizeof(double) * (size_t)n_taps) != cudaSuccess ||
         cudaMalloc(&p->W, sizeof(float) * (size_t)p->nW) != cudaSuccess ||
-        cudaMalloc(&p->fwd_base, sizeof(int) * (size_t)K) != cudaSuccess ||
+        cudaMalloc(&p->fwd_base, sizeof(int) * (size_t)Kf) != cudaSuccess ||
         cudaMalloc(&p->scal, sizeof(double) * 8) != cudaSuccess) {
         cleanup();
         pat_plan_destroy(p);
@@ -241,13 +294,15 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
     static_assert(sizeof(pat_transducer) == 16 * sizeof(double), "descriptor layout");
     pat_status rc = PAT_OK;
     do {
-        if (cudaMemcpyAsync(raw, tx, sizeof(double) * 16 * (size_t)K, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        if (cudaMemcpyAsync(raw, fx, sizeof(double) * 16 * (size_t)Kf, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(p->rows, rows_h.data(), sizeof(int) * (size_t)Kf, cudaMemcpyHostToDevice, s) !=
+                cudaSuccess ||
             cudaMemcpyAsync(p->taps, taps_host, sizeof(double) * (size_t)n_taps, cudaMemcpyHostToDevice, s) !=
                 cudaSuccess) {
             rc = fail(PAT_ERR_CUDA, "pat_plan_create: copy failed");
             break;
         }
-        if (launch_frames(raw, K, grid->origin, grid->pitch, tm.q1, tm.q2, p->tx, s) != cudaSuccess ||
+        if (launch_frames(raw, Kf, grid->origin, grid->pitch, tm.q1, tm.q2, p->tx, s) != cudaSuccess ||
             launch_combine_taps(p->taps, n_taps, params->U, p->W, s) != cudaSuccess) {
             rc = fail(PAT_ERR_CUDA, "pat_plan_create: setup kernels failed");
             break;
@@ -267,22 +322,22 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
         }
         // scan every pair once
         void *sbuf = nullptr;
-        size_t sb = sizeof(long long) * 6 * (size_t)K + 64;
+        size_t sb = sizeof(long long) * 6 * (size_t)Kf + 64;
         if (cudaMalloc(&sbuf, sb) != cudaSuccess) {
             rc = fail(PAT_ERR_CUDA, "pat_plan_create: cudaMalloc failed");
             break;
         }
         ScanOut so;
         so.lo = (long long *)sbuf;
-        so.hi = so.lo + K;
-        so.groups = (unsigned long long *)(so.hi + K);
-        so.bins = so.groups + K;
-        so.clipped = so.bins + K;
-        so.quads = so.clipped + K;
-        so.rmin_bits = so.quads + K;
-        std::vector<long long> hb(6 * (size_t)K + 1);
-        cudaError_t e = launch_scan(p->tx, K, tm, g, so, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), sbuf, sizeof(long long) * (6 * (size_t)K + 1),
+        so.hi = so.lo + Kf;
+        so.groups = (unsigned long long *)(so.hi + Kf);
+        so.bins = so.groups + Kf;
+        so.clipped = so.bins + Kf;
+        so.quads = so.clipped + Kf;
+        so.rmin_bits = so.quads + Kf;
+        std::vector<long long> hb(6 * (size_t)Kf + 1);
+        cudaError_t e = launch_scan(p->tx, Kf, tm, g, so, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), sbuf, sizeof(long long) * (6 * (size_t)Kf + 1),
                                                   cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         cudaFree(sbuf);
@@ -305,10 +360,10 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
         // per-transducer window of the forward difference array: edges of its
         // pairs lie in [lo, hi + 1]; one bin of margin on either side covers
         // the point method's FP32 bin decision at the ends of the range
-        std::vector<int> base((size_t)K);
+        std::vector<int> base((size_t)Kf);
         long long span = 1;
-        for (int k = 0; k < K; ++k) {
-            long long lo = hb[k], hi = hb[K + k];
+        for (int k = 0; k < Kf; ++k) {
+            long long lo = hb[k], hi = hb[Kf + k];
             long long b0 = 0, b1 = 0;
             if (lo <= hi) {
                 b0 = std::min<long long>(std::max<long long>(lo - 1, 0), tm.UL);
@@ -323,32 +378,33 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
                       "device has %d", span, 2 * sizeof(float) * (size_t)span, p->smem_optin);
             break;
         }
-        if (cudaMemcpyAsync(p->fwd_base, base.data(), sizeof(int) * (size_t)K, cudaMemcpyHostToDevice, s) !=
+        if (cudaMemcpyAsync(p->fwd_base, base.data(), sizeof(int) * (size_t)Kf, cudaMemcpyHostToDevice, s) !=
                 cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
             rc = fail(PAT_ERR_CUDA, "pat_plan_create: copy failed");
             break;
         }
-        for (int k = 0; k < K; ++k) {
-            long long lo = hb[k], hi = hb[K + k];
+        // per element (plane facet); conv_clipped counts elements
+        for (int k = 0; k < Kf; ++k) {
+            long long lo = hb[k], hi = hb[Kf + k];
             in.bin_lo = std::min<long long>(in.bin_lo, lo);
             in.bin_hi = std::max<long long>(in.bin_hi, hi);
-            in.area_evals += hb[2 * (size_t)K + k];
-            in.pair_bins += hb[3 * (size_t)K + k];
-            in.clipped_pairs += hb[4 * (size_t)K + k];
-            in.quad_evals += hb[5 * (size_t)K + k];
+            in.area_evals += hb[2 * (size_t)Kf + k];
+            in.pair_bins += hb[3 * (size_t)Kf + k];
+            in.clipped_pairs += hb[4 * (size_t)Kf + k];
+            in.quad_evals += hb[5 * (size_t)Kf + k];
             if (lo + n_lo < 0 || hi + n_lo + n_taps - 1 >= tm.UL) in.conv_clipped++;
         }
-        unsigned long long rb = (unsigned long long)hb[6 * (size_t)K];
+        unsigned long long rb = (unsigned long long)hb[6 * (size_t)Kf];
         memcpy(&in.dist_min, &rb, sizeof(double));
         // work split of the forward geometric kernel: about 8 CTAs per SM in total
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        long long want = (8LL * std::max(sms, 1) + K - 1) / K;
+        long long want = (8LL * std::max(sms, 1) + Kf - 1) / Kf;
         long long maxc = std::max(1LL, g.nbricks / kWarpsPerBlock);
         p->fwd_chunks = (int)std::max(1LL, std::min(want, maxc));
         p->adj_wpb = kWarpsPerBlock;
-        in.fwd_blocks = (long long)p->fwd_chunks * K;
+        in.fwd_blocks = (long long)p->fwd_chunks * Kf;
         in.adj_blocks = (g.nbricks + p->adj_wpb - 1) / p->adj_wpb;
         if (!(in.dist_min >= kappa)) {
             rc = fail(PAT_ERR_GEOMETRY, "dist_min = %.6g m < kappa = %.6g m (Assumption 1(iii))", in.dist_min, kappa);
@@ -386,6 +442,7 @@ extern "C" pat_status pat_plan_destroy(pat_plan *p)
     cudaFree(p->taps);
     cudaFree(p->W);
     cudaFree(p->fwd_base);
+    cudaFree(p->rows);
     cudaFree(p->scal);
     cudaFree(p->tc_fwd_tab);
     cudaFree(p->tc_adj_tab);
@@ -455,7 +512,8 @@ static pat_status check_ws(const pat_plan *p, void *ws, size_t bytes, size_t nee
 static pat_status enqueue_forward(pat_plan *p, const float *x, float *s, float *f, void *ws, cudaStream_t st)
 {
     double *D = (double *)ws;
-    CK(launch_fwd_geom(p->tx, p->K, p->kind_all, p->tm, p->g, x, D, p->fwd_chunks, p->fwd_base, p->fwd_span, st));
+    CK(launch_fwd_geom(p->tx, p->Kf, p->K, p->rows, p->kind_all, p->tm, p->g, x, D, p->fwd_chunks, p->fwd_base,
+                       p->fwd_span, st));
     int mode = p->tm.method == PAT_METHOD_POINT ? 1 : 0;
     if (p->tc && s) {
         float *fw = (float *)((char *)ws + ws_D(p));
@@ -478,7 +536,7 @@ static pat_status enqueue_adjoint(pat_plan *p, const float *in, int from_v, floa
         from_v = 1;
     }
     CK(launch_adj_conv(in, from_v, p->W, p->nW, p->n_lo, p->tm, mode, p->K, ws, st));
-    CK(launch_adj_geom(p->tx, p->K, p->kind_all, p->tm, p->g, ws, z, st, p->adj_wpb));
+    CK(launch_adj_geom(p->tx, p->Kf, p->rows, p->kind_all, p->tm, p->g, ws, z, st, p->adj_wpb));
     return PAT_OK;
 }
 
@@ -563,7 +621,8 @@ extern "C" pat_status pat_forward_dc(pat_plan *p, const float *x, const double *
     if (st != PAT_OK) return st;
     cudaStream_t cs = (cudaStream_t)stream;
     double *Dg = (double *)ws, *Dd = (double *)((char *)ws + ws_D(p));
-    CK(launch_fwd_geom_dc(p->tx, p->K, p->kind_all, p->tm, p->g, x, Dg, Dd, p->fwd_chunks, p->fwd_base, p->fwd_span,
+    CK(launch_fwd_geom_dc(p->tx, p->Kf, p->K, p->rows, p->kind_all, p->tm, p->g, x, Dg, Dd, p->fwd_chunks, p->fwd_base,
+                          p->fwd_span,
                           cs));
     CK(launch_fwd_dc_epilogue(Dg, Dd, p->W, dtaps, p->T, p->nW, p->n_lo, p->tm, p->K, ds, cs));
     return PAT_OK;
@@ -825,7 +884,8 @@ extern "C" pat_status pat_plan_autotune(pat_plan *p, const float *x, void *ws, s
         if (std::find(tried.begin(), tried.end(), c) != tried.end()) continue;
         tried.push_back(c);
         const float t = timed([&] {
-            return launch_fwd_geom(p->tx, p->K, p->kind_all, p->tm, p->g, x, D, (int)c, p->fwd_base, p->fwd_span, cs);
+            return launch_fwd_geom(p->tx, p->Kf, p->K, p->rows, p->kind_all, p->tm, p->g, x, D, (int)c, p->fwd_base,
+                                   p->fwd_span, cs);
         });
         if (t < 0.f) {
             cudaEventDestroy(e0);
@@ -843,7 +903,8 @@ extern "C" pat_status pat_plan_autotune(pat_plan *p, const float *x, void *ws, s
     float best_a = 3.0e38f;
     CK(cudaMemsetAsync(ws, 0, ws_P(p), cs));
     for (int wpb : {2, 4, 8}) {
-        const float t = timed([&] { return launch_adj_geom(p->tx, p->K, p->kind_all, p->tm, p->g, ws, z, cs, wpb); });
+        const float t =
+            timed([&] { return launch_adj_geom(p->tx, p->Kf, p->rows, p->kind_all, p->tm, p->g, ws, z, cs, wpb); });
         if (t < 0.f) {
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
@@ -858,7 +919,7 @@ extern "C" pat_status pat_plan_autotune(pat_plan *p, const float *x, void *ws, s
     cudaEventDestroy(e1);
     p->fwd_chunks = best_c;
     p->adj_wpb = best_w;
-    p->info.fwd_blocks = (long long)best_c * p->K;
+    p->info.fwd_blocks = (long long)best_c * p->Kf;
     p->info.adj_blocks = (p->g.nbricks + best_w - 1) / best_w;
     return PAT_OK;
 }

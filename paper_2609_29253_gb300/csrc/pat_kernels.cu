@@ -232,11 +232,14 @@ struct FwdPointSink {
 // base[k]: first fine-bin edge of transducer k's window (from the plan-time
 // scan); span: window length shared by all k.  Dg: [K][UL + 1] doubles, zeroed
 // by the launcher; each CTA adds its window into row k.
+// rows[k]: the signal row that element (or plane facet) k adds into; with
+// exclusive != 0 every row has one element, and a CTA that covers its whole
+// element stores its window instead of adding it.
 template <int METHOD, int KIND>
 __global__ void __launch_bounds__(kThreads, 3) fwd_geom_kernel(const TxDev *__restrict__ tx, TimeDev tm, GridDev g,
                                                             const float *__restrict__ x, double *__restrict__ Dg,
                                                             int bricks_per_cta, const int *__restrict__ base,
-                                                            int span)
+                                                            int span, const int *__restrict__ rows, int exclusive)
 {
     extern __shared__ float sD[];
     __shared__ float glx[kGLTable], glw[kGLTable];
@@ -263,15 +266,15 @@ __global__ void __launch_bounds__(kThreads, 3) fwd_geom_kernel(const TxDev *__re
                 point_pair<KIND>(t, tm, ix, iy, iz, s);
             } else {
                 FwdSurfaceSink s{win, xv, 0.f};
-                surface_pair<KIND, false>(t, tm, ix, iy, iz, s, glx, glw);
+                surface_pair<KIND, false, METHOD == PAT_METHOD_TRAPEZOID>(t, tm, ix, iy, iz, s, glx, glw);
             }
         }
         __syncwarp();
     }
     __syncthreads();
-    double *row = Dg + (size_t)k * n + win.base;
+    double *row = Dg + (size_t)rows[k] * n + win.base;
     const int m = win.top - win.base + 1;
-    if (gridDim.x == 1) {
+    if (gridDim.x == 1 && exclusive) {
         for (int i = threadIdx.x; i < m; i += blockDim.x) row[i] = (double)win.hi[i] + (double)win.lo[i];
     } else {
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -288,7 +291,8 @@ template <int KIND>
 __global__ void __launch_bounds__(kThreads) fwd_geom_dc_kernel(const TxDev *__restrict__ tx, TimeDev tm, GridDev g,
                                                                const float *__restrict__ x, double *__restrict__ Dg,
                                                                double *__restrict__ Dd, int bricks_per_cta,
-                                                               const int *__restrict__ base, int span)
+                                                               const int *__restrict__ base, int span,
+                                                               const int *__restrict__ rows, int exclusive)
 {
     extern __shared__ float sD[];
     __shared__ float glx[kGLTable], glw[kGLTable];
@@ -318,11 +322,11 @@ __global__ void __launch_bounds__(kThreads) fwd_geom_dc_kernel(const TxDev *__re
     }
     __syncthreads();
     const int m = win.top - win.base + 1;
-    double *row = Dg + (size_t)k * n + win.base, *rowd = Dd + (size_t)k * n + win.base;
+    double *row = Dg + (size_t)rows[k] * n + win.base, *rowd = Dd + (size_t)rows[k] * n + win.base;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         const double v = (double)win.hi[i] + (double)win.lo[i];
         const double vd = (double)wind.hi[i] + (double)wind.lo[i];
-        if (gridDim.x == 1) {
+        if (gridDim.x == 1 && exclusive) {
             row[i] = v;
             rowd[i] = vd;
         } else {
@@ -569,7 +573,7 @@ struct AdjPointSink {
 template <int METHOD, int KIND>
 __global__ void __launch_bounds__(kThreads, 3) adj_geom_kernel(const TxDev *__restrict__ tx, int K, TimeDev tm,
                                                             GridDev g, const void *__restrict__ Pv,
-                                                            float *__restrict__ z)
+                                                            float *__restrict__ z, const int *__restrict__ rows)
 {
     __shared__ float glx[kGLTable], glw[kGLTable];
     gl_fill(glx, glw, threadIdx.x);
@@ -585,12 +589,13 @@ __global__ void __launch_bounds__(kThreads, 3) adj_geom_kernel(const TxDev *__re
         if (ok) {
             const TxDev &t = tx[k];
             if (METHOD == PAT_METHOD_POINT) {
-                AdjPointSink s{(const float *)Pv + (size_t)k * stride, tm.UL, 0.f};
+                AdjPointSink s{(const float *)Pv + (size_t)rows[k] * stride, tm.UL, 0.f};
                 point_pair<KIND>(t, tm, ix, iy, iz, s);
                 acc += (double)s.acc;
             } else {
-                AdjSurfaceSink s{(const float2 *)Pv + (size_t)k * stride, tm.UL, 0.f, make_float2(0.f, 0.f), false};
-                surface_pair<KIND, false>(t, tm, ix, iy, iz, s, glx, glw);
+                AdjSurfaceSink s{(const float2 *)Pv + (size_t)rows[k] * stride, tm.UL, 0.f, make_float2(0.f, 0.f),
+                                 false};
+                surface_pair<KIND, false, METHOD == PAT_METHOD_TRAPEZOID>(t, tm, ix, iy, iz, s, glx, glw);
                 acc += (double)s.acc;
             }
         }
@@ -832,17 +837,25 @@ cudaError_t launch_scan(const TxDev *tx, int K, const TimeDev &tm, const GridDev
 
 // One instantiation per (method, element kind); kind kKindAny reads it from
 // each descriptor.
+struct FacetArgs {
+    const int *rows;
+    int exclusive;
+};
+
 template <int METHOD, int KIND>
 static cudaError_t fwd_geom_go(dim3 grid, size_t smem, cudaStream_t st, const TxDev *tx, const TimeDev &tm,
-                               const GridDev &g, const float *x, double *Dg, int bpc, const int *base, int span)
+                               const GridDev &g, const float *x, double *Dg, int bpc, const int *base, int span,
+                               FacetArgs fa)
 {
     set_smem_attr((const void *)fwd_geom_kernel<METHOD, KIND>, smem);
-    fwd_geom_kernel<METHOD, KIND><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, bpc, base, span);
+    fwd_geom_kernel<METHOD, KIND><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, bpc, base, span, fa.rows,
+                                                                fa.exclusive);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fwd_geom(const TxDev *tx, int K, int kind, const TimeDev &tm, const GridDev &g, const float *x,
-                            double *Dg, int chunks, const int *base, int span, cudaStream_t st)
+cudaError_t launch_fwd_geom(const TxDev *tx, int Kf, int K, const int *rows, int kind, const TimeDev &tm,
+                            const GridDev &g, const float *x, double *Dg, int chunks, const int *base, int span,
+                            cudaStream_t st)
 {
     size_t smem = 2 * sizeof(float) * (size_t)span;
     long long bpc = (g.nbricks + chunks - 1) / chunks;
@@ -850,22 +863,31 @@ cudaError_t launch_fwd_geom(const TxDev *tx, int K, int kind, const TimeDev &tm,
     unsigned gx = (unsigned)((g.nbricks + bpc - 1) / bpc);
     cudaError_t e = cudaMemsetAsync(Dg, 0, sizeof(double) * (size_t)(tm.UL + 1) * K, st);
     if (e != cudaSuccess) return e;
-    const dim3 grid(gx, (unsigned)K);
+    const dim3 grid(gx, (unsigned)Kf);
+    const FacetArgs fa{rows, Kf == K ? 1 : 0};
     const int b = (int)bpc;
     if (tm.method == PAT_METHOD_POINT) {
-        if (kind == PAT_PLANE) return fwd_geom_go<PAT_METHOD_POINT, PAT_PLANE>(grid, smem, st, tx, tm, g, x, Dg, b, base, span);
+        if (kind == PAT_PLANE) return fwd_geom_go<PAT_METHOD_POINT, PAT_PLANE>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
         if (kind == PAT_CYLINDER)
-            return fwd_geom_go<PAT_METHOD_POINT, PAT_CYLINDER>(grid, smem, st, tx, tm, g, x, Dg, b, base, span);
-        return fwd_geom_go<PAT_METHOD_POINT, kKindAny>(grid, smem, st, tx, tm, g, x, Dg, b, base, span);
+            return fwd_geom_go<PAT_METHOD_POINT, PAT_CYLINDER>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
+        return fwd_geom_go<PAT_METHOD_POINT, kKindAny>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
     }
-    if (kind == PAT_PLANE) return fwd_geom_go<PAT_METHOD_SURFACE, PAT_PLANE>(grid, smem, st, tx, tm, g, x, Dg, b, base, span);
+    if (tm.method == PAT_METHOD_TRAPEZOID) {
+        if (kind == PAT_PLANE)
+            return fwd_geom_go<PAT_METHOD_TRAPEZOID, PAT_PLANE>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
+        if (kind == PAT_CYLINDER)
+            return fwd_geom_go<PAT_METHOD_TRAPEZOID, PAT_CYLINDER>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
+        return fwd_geom_go<PAT_METHOD_TRAPEZOID, kKindAny>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
+    }
+    if (kind == PAT_PLANE) return fwd_geom_go<PAT_METHOD_SURFACE, PAT_PLANE>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
     if (kind == PAT_CYLINDER)
-        return fwd_geom_go<PAT_METHOD_SURFACE, PAT_CYLINDER>(grid, smem, st, tx, tm, g, x, Dg, b, base, span);
-    return fwd_geom_go<PAT_METHOD_SURFACE, kKindAny>(grid, smem, st, tx, tm, g, x, Dg, b, base, span);
+        return fwd_geom_go<PAT_METHOD_SURFACE, PAT_CYLINDER>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
+    return fwd_geom_go<PAT_METHOD_SURFACE, kKindAny>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
 }
 
-cudaError_t launch_fwd_geom_dc(const TxDev *tx, int K, int kind, const TimeDev &tm, const GridDev &g, const float *x,
-                               double *Dg, double *Dd, int chunks, const int *base, int span, cudaStream_t st)
+cudaError_t launch_fwd_geom_dc(const TxDev *tx, int Kf, int K, const int *rows, int kind, const TimeDev &tm,
+                               const GridDev &g, const float *x, double *Dg, double *Dd, int chunks, const int *base,
+                               int span, cudaStream_t st)
 {
     size_t smem = 4 * sizeof(float) * (size_t)span;
     long long bpc = (g.nbricks + chunks - 1) / chunks;
@@ -875,17 +897,21 @@ cudaError_t launch_fwd_geom_dc(const TxDev *tx, int K, int kind, const TimeDev &
     cudaError_t e = cudaMemsetAsync(Dg, 0, bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(Dd, 0, bytes, st);
     if (e != cudaSuccess) return e;
-    const dim3 grid(gx, (unsigned)K);
+    const dim3 grid(gx, (unsigned)Kf);
+    const int excl = Kf == K ? 1 : 0;
     const void *fn = kind == PAT_PLANE      ? (const void *)fwd_geom_dc_kernel<PAT_PLANE>
                      : kind == PAT_CYLINDER ? (const void *)fwd_geom_dc_kernel<PAT_CYLINDER>
                                             : (const void *)fwd_geom_dc_kernel<kKindAny>;
     set_smem_attr(fn, smem);
     if (kind == PAT_PLANE)
-        fwd_geom_dc_kernel<PAT_PLANE><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, Dd, (int)bpc, base, span);
+        fwd_geom_dc_kernel<PAT_PLANE><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, Dd, (int)bpc, base, span, rows,
+                                                                                   excl);
     else if (kind == PAT_CYLINDER)
-        fwd_geom_dc_kernel<PAT_CYLINDER><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, Dd, (int)bpc, base, span);
+        fwd_geom_dc_kernel<PAT_CYLINDER><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, Dd, (int)bpc, base, span, rows,
+                                                                                   excl);
     else
-        fwd_geom_dc_kernel<kKindAny><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, Dd, (int)bpc, base, span);
+        fwd_geom_dc_kernel<kKindAny><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, Dd, (int)bpc, base, span, rows,
+                                                                                   excl);
     return cudaGetLastError();
 }
 
@@ -916,21 +942,26 @@ cudaError_t launch_adj_conv(const float *s, int from_v, const float *W, int nW, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_geom(const TxDev *tx, int K, int kind, const TimeDev &tm, const GridDev &g, const void *P,
-                            float *z, cudaStream_t st, int wpb)
+cudaError_t launch_adj_geom(const TxDev *tx, int K, const int *rows, int kind, const TimeDev &tm, const GridDev &g,
+                            const void *P, float *z, cudaStream_t st, int wpb)
 {
     wpb = wpb == 4 || wpb == 2 ? wpb : kWarpsPerBlock; // warps (bricks) per CTA
     const unsigned grid = (unsigned)((g.nbricks + wpb - 1) / wpb), thr = 32u * wpb;
     if (tm.method == PAT_METHOD_POINT) {
-        if (kind == PAT_PLANE) adj_geom_kernel<PAT_METHOD_POINT, PAT_PLANE><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z);
+        if (kind == PAT_PLANE) adj_geom_kernel<PAT_METHOD_POINT, PAT_PLANE><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z, rows);
         else if (kind == PAT_CYLINDER)
-            adj_geom_kernel<PAT_METHOD_POINT, PAT_CYLINDER><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z);
-        else adj_geom_kernel<PAT_METHOD_POINT, kKindAny><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z);
+            adj_geom_kernel<PAT_METHOD_POINT, PAT_CYLINDER><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z, rows);
+        else adj_geom_kernel<PAT_METHOD_POINT, kKindAny><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z, rows);
+    } else if (tm.method == PAT_METHOD_TRAPEZOID) {
+        if (kind == PAT_PLANE) adj_geom_kernel<PAT_METHOD_TRAPEZOID, PAT_PLANE><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z, rows);
+        else if (kind == PAT_CYLINDER)
+            adj_geom_kernel<PAT_METHOD_TRAPEZOID, PAT_CYLINDER><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z, rows);
+        else adj_geom_kernel<PAT_METHOD_TRAPEZOID, kKindAny><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z, rows);
     } else {
-        if (kind == PAT_PLANE) adj_geom_kernel<PAT_METHOD_SURFACE, PAT_PLANE><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z);
+        if (kind == PAT_PLANE) adj_geom_kernel<PAT_METHOD_SURFACE, PAT_PLANE><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z, rows);
         else if (kind == PAT_CYLINDER)
-            adj_geom_kernel<PAT_METHOD_SURFACE, PAT_CYLINDER><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z);
-        else adj_geom_kernel<PAT_METHOD_SURFACE, kKindAny><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z);
+            adj_geom_kernel<PAT_METHOD_SURFACE, PAT_CYLINDER><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z, rows);
+        else adj_geom_kernel<PAT_METHOD_SURFACE, kKindAny><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z, rows);
     }
     return cudaGetLastError();
 }

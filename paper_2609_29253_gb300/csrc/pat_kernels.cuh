@@ -19,22 +19,26 @@ cudaError_t launch_frames(const double *raw, int K, const double *origin, double
 cudaError_t launch_scan(const TxDev *tx, int K, const TimeDev &tm, const GridDev &g, ScanOut s, cudaStream_t st);
 // Dg: [K][UL + 1] doubles; base[k], span: fine-bin window of each transducer.
 // kind: PAT_PLANE or PAT_CYLINDER when every descriptor has it, else kKindAny.
-cudaError_t launch_fwd_geom(const TxDev *tx, int K, int kind, const TimeDev &tm, const GridDev &g, const float *x,
-                            double *Dg, int chunks, const int *base, int span, cudaStream_t st);
+// Kf elements (or plane facets) add into K signal rows, element k into
+// rows[k] (Kf == K: one element per row).
+cudaError_t launch_fwd_geom(const TxDev *tx, int Kf, int K, const int *rows, int kind, const TimeDev &tm,
+                            const GridDev &g, const float *x, double *Dg, int chunks, const int *base, int span,
+                            cudaStream_t st);
 // in: doubles for mode 0 / 1 (difference array, histogram), floats for mode 2 (f)
 cudaError_t launch_fwd_epilogue(const void *in, int in_stride, const float *W, int nW, int n_lo, const TimeDev &tm,
                                 int mode, int K, float *s, float *f_out, cudaStream_t st);
 cudaError_t launch_adj_conv(const float *in, int from_v, const float *W, int nW, int n_lo, const TimeDev &tm, int mode,
                             int K, void *out, cudaStream_t st);
 // wpb: warps (4x4x2 voxel bricks) per CTA, 2, 4 or 8
-cudaError_t launch_adj_geom(const TxDev *tx, int K, int kind, const TimeDev &tm, const GridDev &g, const void *P,
-                            float *z, cudaStream_t st, int wpb = kWarpsPerBlock);
+cudaError_t launch_adj_geom(const TxDev *tx, int K, const int *rows, int kind, const TimeDev &tm, const GridDev &g,
+                            const void *P, float *z, cudaStream_t st, int wpb = kWarpsPerBlock);
 // dc: dh-bar/dc instead of h-bar
 cudaError_t launch_taps(int rbf, int eir, double kappa, double c, const double *e, double ufs, int n_lo, int T,
                         double *taps, cudaStream_t st, bool dc = false);
 // speed-of-sound derivative: difference arrays of f and of df/dc (fixed bins)
-cudaError_t launch_fwd_geom_dc(const TxDev *tx, int K, int kind, const TimeDev &tm, const GridDev &g, const float *x,
-                               double *Dg, double *Dd, int chunks, const int *base, int span, cudaStream_t st);
+cudaError_t launch_fwd_geom_dc(const TxDev *tx, int Kf, int K, const int *rows, int kind, const TimeDev &tm,
+                               const GridDev &g, const float *x, double *Dg, double *Dd, int chunks, const int *base,
+                               int span, cudaStream_t st);
 cudaError_t launch_fwd_dc_epilogue(const double *Dg, const double *Dd, const float *W, const double *dtaps, int T,
                                    int nW, int n_lo, const TimeDev &tm, int K, float *ds, cudaStream_t st);
 cudaError_t launch_combine_taps(const double *taps, int T, int U, float *W, cudaStream_t st);

@@ -43,6 +43,7 @@ PLANE = 0
 CYLINDER = 1
 METHOD_SURFACE = 0
 METHOD_POINT = 1
+METHOD_TRAPEZOID = 2
 RBF_BUMP = 0  # (1 - r^2/k^2)^2
 RBF_CONE = 1  # 1 - r/k
 RBF_WENDLAND = 2  # (1 - r/k)^2

@@ -95,6 +95,37 @@ def test_cylinder_surface(api, orc, dl):
     _run(api, orc, W.small_cylinder(n_vox=12, n_angles=4, n_el=3, dl=dl))
 
 
+@pytest.mark.parametrize("dl", [1, 11])
+def test_cylinder_trapezoid(api, orc, dl):
+    """The trapezoidal arc integral (Eq. trapezoid_Il) against the oracle's
+    own trapezoidal areas, all stages, and its distance to the exact areas."""
+    w = W.small_cylinder(n_vox=12, n_angles=4, n_el=3, dl=dl).with_(method=W.METHOD_TRAPEZOID)
+    _, s, s_ref = _run(api, orc, w)
+    s_ex, _ = orc.forward(w.with_(method=W.METHOD_SURFACE), orc.taps_for(w), w.x.astype(np.float32).astype(np.float64))
+    assert 0.0 < rel(s_ref, s_ex) < 0.2
+
+
+@pytest.mark.parametrize("n_planes", [1, 8, 30])
+def test_cylinder_piecewise_planes(api, orc, n_planes):
+    """Piecewise-Planes (Sec. 4.3): the library's own tangent-plane expansion
+    against the oracle's, A and A^T, each plane's signal summed into its
+    element's row."""
+    w = W.small_cylinder(n_vox=9, n_angles=3, n_el=2)
+    taps = orc.taps_for(w)
+    plan = api.Plan(w, taps=taps, piecewise_planes=n_planes)
+    x32 = w.x.astype(np.float32)
+    s = plan.forward(torch.from_numpy(x32).cuda()).cpu().numpy()
+    s_ref, _ = orc.piecewise_planes_forward(w, taps, x32.astype(np.float64), n_planes)
+    assert rel(s, s_ref) <= SURF_TOL, rel(s, s_ref)
+    y = np.random.default_rng(6).standard_normal(s.shape).astype(np.float32)
+    z = plan.adjoint(torch.from_numpy(y).cuda()).cpu().numpy()
+    z_ref, _ = orc.piecewise_planes_adjoint(w, taps, y.astype(np.float64), n_planes)
+    assert rel(z, z_ref) <= SURF_TOL, rel(z, z_ref)
+    if n_planes == 30:  # the approximation itself, against the exact cylinder
+        s_ex, _ = orc.forward(w, taps, x32.astype(np.float64))
+        assert rel(s_ref, s_ex) < 0.2
+
+
 def test_cylinder_point(api, orc):
     w = W.small_cylinder(n_vox=8, n_angles=3, n_el=2)
     _run(api, orc, w.with_(method=W.METHOD_POINT, q1=16, q2=4), tol=POINT_TOL)
