@@ -361,6 +361,34 @@ def c5_line(api, dev, n_pos):
             "mean_bins_per_pair": plan.info["pair_bins"] / pairs}
 
 
+def exp1_line(api, dev):
+    """The paper's Experiment 1 system (fine grid: 98,415 voxels x 215
+    cylindrical elements, 2688 samples at 62.5 MHz): one A plus one A^T with
+    the exact areas, the trapezoidal approximation, Piecewise-Planes with 30
+    planes and the point method with 25 x 25 points (Q = 625), each with its
+    distance to the exact A x.  The paper's own per-iteration times (A100,
+    FP64, one A and one A^T assumed per iteration) are context, not targets."""
+    import torch
+
+    w = W.exp1("fine")
+    x = torch.from_numpy(w.x).to(dev)
+    taps = api.system_taps(w, dev)
+    ops = {"exact": api.Plan(w, taps=taps, device=dev),
+           "trapezoidal": api.Plan(w.with_(method=W.METHOD_TRAPEZOID), taps=taps, device=dev),
+           "piecewise_planes_30": api.Plan(w, taps=taps, piecewise_planes=30, device=dev),
+           "point_625": api.Plan(w.with_(method=W.METHOD_POINT, q1=25, q2=25), taps=taps, device=dev)}
+    s_ex = ops["exact"].forward(x)
+    out = {"workload": w.name, "pairs_per_application": w.N * w.K}
+    for name, p in ops.items():
+        s = p.forward(x)
+        z = torch.empty(w.N, device=dev)
+        t = cuda_ms(lambda: (p.forward(x, out=s), p.adjoint(s, out=z)), reps=3)
+        out[name] = {"ms_A_plus_AT": t, "rel_l2_vs_exact": rel_l2(s, s_ex)}
+    out["paper_a100_fp64_ms_per_iteration"] = {"exact": 2021, "lut": 192, "trapezoidal": 145, "point_625": 533,
+                                               "piecewise_planes_30": 1256}
+    return out
+
+
 def config(args, w):
     grid = "" if args.grid == 128 else f" [reduced grid {args.grid}^3 for profiling]"
     return {"workload": "c2: 128^3 voxels @ 0.1 mm, 128-element cylindrical array (R 20 mm, 10 mm elevation, "
@@ -494,6 +522,7 @@ def main():
         extras["c3_precision_split"] = c3_line(api, dev, args.c3_positions)
         if args.c5_positions > 0:
             extras["c5_full_scale_subset"] = c5_line(api, dev, args.c5_positions)
+        extras["exp1_operators"] = exp1_line(api, dev)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,

@@ -283,6 +283,20 @@ def tube_phantom(n, origin, pitch, n_tubes, seed, r_vox=(1.0, 3.0), inner=0.8, s
     return x.astype(np.float32)
 
 
+def rod_phantom(n, origin, pitch, spacing=0.9e-3, n_rods=7, r_xy=0.1125e-3, r_z=0.2625e-3):
+    """A n_rods x n_rods grid of rods centred on the z = 0 plane, spacing
+    apart, each with the paraboloidal profile (1 - (dx^2 + dy^2)/r_xy^2 -
+    dz^2/r_z^2)_+ (support 225 x 225 x 525 um with the defaults)."""
+    pts = voxel_centres(n, origin, pitch)
+    c = (np.arange(n_rods) - (n_rods - 1) / 2.0) * spacing
+    x = np.zeros(len(pts))
+    for cx in c:
+        for cy in c:
+            v = 1.0 - ((pts[:, 0] - cx) ** 2 + (pts[:, 1] - cy) ** 2) / r_xy ** 2 - pts[:, 2] ** 2 / r_z ** 2
+            x = np.maximum(x, np.clip(v, 0.0, None))
+    return x.astype(np.float32)
+
+
 # --------------------------------------------------------------------------
 # presets
 # --------------------------------------------------------------------------
@@ -370,6 +384,28 @@ def c4_problem(p, n_range=(48, 160), k_range=(1024, 8192), seed_base=1000):
     x = tube_phantom((n, n, n), origin, pitch, int(rng.integers(5, 16)), seed_base + p)
     return _make(f"c4 problem {p}: {n}^3 @ 0.1 mm, {len(tx)} {kind} positions, L={L} @ 40 MHz", (n, n, n), pitch, tx,
                  1500.0, 40e6, t0, L, 11, 1.5 * pitch, gauss_sine_eir(5e6), x=x)
+
+
+def exp1(grid="fine", method=METHOD_SURFACE, q=(25, 25)):
+    """The paper's controlled synthetic study (Sec. 5.2): 215 cylindrically
+    focused elements (R 25 mm, 7.5 mm elevation aperture, 0.25 mm wide)
+    rotated about their focal line at 43 azimuths, at 5 positions spanning
+    36.7 mm along it; a 6 x 6 x 1.05 mm volume on the fine 81 x 81 x 15 grid
+    (75 um) or the coarse 27 x 27 x 5 grid (225 um); 7 x 7 rods; 2688 samples
+    at 62.5 MHz from t = 0, U 11, dl = U."""
+    n, pitch = ((81, 81, 15), 75e-6) if grid == "fine" else ((27, 27, 5), 225e-6)
+    rows = []
+    for zj in np.linspace(-18.35e-3, 18.35e-3, 5):
+        for m in range(43):
+            a = 2 * math.pi * m / 43
+            rows.append(cylinder_row(np.array([0.0, 0.0, zj]), np.array([0.0, 0.0, 1.0]),
+                                     np.array([math.cos(a), math.sin(a), 0.0]), 25e-3, math.asin(3.75 / 25.0),
+                                     0.125e-3))
+    origin = centred_origin(n, pitch)
+    x = rod_phantom(n, origin, pitch)
+    return _make(f"exp1 ({grid}): {n[0]}x{n[1]}x{n[2]} @ {pitch * 1e6:.0f} um, 215 cylindrical elements, "
+                 f"L=2688 @ 62.5 MHz", n, pitch, np.array(rows), 1500.0, 62.5e6, 0.0, 2688, 11, 1.5 * pitch,
+                 gauss_sine_eir(5e6, frac_bw=1.6), x=x, method=method, q=q if method == METHOD_POINT else (0, 0))
 
 
 def small_cylinder(n_vox=12, n_angles=4, n_el=4, seed=0, dl=None, L=None):
