@@ -41,12 +41,12 @@ N_ANGLES = 180
 # cylinder path: 2 per FFMA, 1 per FADD / FMUL, 4 per FFMA2, 2 per FADD2 /
 # FMUL2 (MUFU operations not counted), from the instruction counters of one
 # adj_geom_kernel launch on the c2 geometry (64^3 grid, 128 positions,
-# 1.450e9 evaluations): 169.7 (170 for the forward kernel).
-FLOPS_PER_QUAD_EVAL = 170
+# 1.450e9 evaluations): 165.5 (166.4 for the forward kernel).
+FLOPS_PER_QUAD_EVAL = 166
 # DRAM read + write bytes of one adj_geom_kernel launch of the default
 # workload (128^3 x 512 positions), one-pass ncu capture of this kernel
-# version (29.06 MB read + 12.41 MB written).
-ADJ_TRAFFIC_BYTES = 41.47e6
+# version (29.38 MB read + 16.85 MB written).
+ADJ_TRAFFIC_BYTES = 46.23e6
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
