@@ -159,6 +159,12 @@ __global__ void scan_kernel(const TxDev *__restrict__ tx, TimeDev tm, GridDev g,
 // ---------------------------------------------------------------------------
 // forward geometric assembly
 // ---------------------------------------------------------------------------
+// The forward window of fwd_geom_kernel is an FP64 array in shared memory
+// (span doubles): every group adds the exact difference of two consecutive
+// FP32 shares with one FP64 atomic, so the long prefix sum of the epilogue
+// does not pile up FP32 rounding.  The derivative kernel keeps two windows
+// and accumulates each as an FP32 pair, below.
+//
 // Compensated accumulation in shared memory: hi[i] takes the FP32 atomic sum,
 // lo[i] the exact rounding error of every addition (recomputed from the value
 // the atomic returns: FP32 atomic addition rounds to nearest even), plus any
@@ -188,13 +194,12 @@ struct FwdSurfaceSink {
     __device__ __forceinline__ void group(int e0, int, float val, float)
     {
         const float v = x * val;
-        const float2 dv = ff_two_sum(v, -prev); // exact difference of consecutive group values
-        if (dv.x != 0.f) acc2(w.hi, w.lo, w.idx(e0), dv.x, dv.y);
+        if (v != prev) atomicAdd((double *)w.hi + w.idx(e0), (double)v - (double)prev);
         prev = v;
     }
     __device__ __forceinline__ void finish(int end)
     {
-        if (prev != 0.f) acc2(w.hi, w.lo, w.idx(end), -prev, 0.f);
+        if (prev != 0.f) atomicAdd((double *)w.hi + w.idx(end), -(double)prev);
     }
 };
 
@@ -225,7 +230,7 @@ struct FwdPointSink {
     float x;
     __device__ __forceinline__ void point(int b, float wt)
     {
-        if (b >= w.base && b <= w.top && b < UL) acc2(w.hi, w.lo, b - w.base, x * wt, 0.f);
+        if (b >= w.base && b <= w.top && b < UL) atomicAdd((double *)w.hi + (b - w.base), (double)(x * wt));
     }
 };
 
@@ -245,9 +250,9 @@ __global__ void __launch_bounds__(kThreads, 3) fwd_geom_kernel(const TxDev *__re
     __shared__ float glx[kGLTable], glw[kGLTable];
     const int k = blockIdx.y;
     const int n = tm.UL + 1;
-    BinWindow win;
+    BinWindow win; // span doubles at sD (the FP64 window, see FwdSurfaceSink)
     win.hi = sD;
-    win.lo = sD + span;
+    win.lo = nullptr;
     win.base = base[k];
     win.top = min(tm.UL, win.base + span - 1);
     for (int b = threadIdx.x; b < 2 * span; b += blockDim.x) sD[b] = 0.f;
@@ -274,11 +279,12 @@ __global__ void __launch_bounds__(kThreads, 3) fwd_geom_kernel(const TxDev *__re
     __syncthreads();
     double *row = Dg + (size_t)rows[k] * n + win.base;
     const int m = win.top - win.base + 1;
+    const double *wd = (const double *)sD;
     if (gridDim.x == 1 && exclusive) {
-        for (int i = threadIdx.x; i < m; i += blockDim.x) row[i] = (double)win.hi[i] + (double)win.lo[i];
+        for (int i = threadIdx.x; i < m; i += blockDim.x) row[i] = wd[i];
     } else {
         for (int i = threadIdx.x; i < m; i += blockDim.x) {
-            const double v = (double)win.hi[i] + (double)win.lo[i];
+            const double v = wd[i];
             if (v != 0.0) atomicAdd(&row[i], v);
         }
     }
