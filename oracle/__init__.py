@@ -60,7 +60,12 @@ def lib():
             L.oracle_pair_bin_areas.restype = C.c_int64
             L.oracle_pair_bin_areas.argtypes = [_D, _D, _D, _I32, C.POINTER(C.c_int64), _D, C.c_int64]
             L.oracle_pair_bin_areas_m.restype = C.c_int64
-            L.oracle_pair_bin_areas_m.argtypes = [_D, _D, _D, _I32, C.c_int, C.POINTER(C.c_int64), _D, C.c_int64]
+            L.oracle_pair_bin_areas_m.argtypes = [_D, _D, _D, _I32, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int64),
+                                                  _D, C.c_int64]
+            L.oracle_ellip_e_lut.restype = C.c_double
+            L.oracle_ellip_e_lut.argtypes = [C.c_double, C.c_double, C.c_int, C.c_int]
+            L.oracle_lut_node.restype = C.c_double
+            L.oracle_lut_node.argtypes = [C.c_int, C.c_int]
             L.oracle_pair_range.restype = C.c_int
             L.oracle_pair_range.argtypes = [_D, _D, _D]
             geo = [_I32, _D, C.c_double, _D, C.c_int, _D, _I32, C.c_int, C.c_int, C.c_int]
@@ -188,23 +193,25 @@ def h_value(rbf_kind, kappa, eir_kind, eir_par, c, t, panels=3):
                                 np.ascontiguousarray(eir_par, dtype=np.float64), float(c), int(panels), float(t))
 
 
-METHOD_SURFACE, METHOD_POINT, METHOD_TRAPEZOID = 0, 1, 2
+METHOD_SURFACE, METHOD_POINT, METHOD_TRAPEZOID, METHOD_LUT = 0, 1, 2, 3
 
 
-def pair_bin_areas(tx_row, xi, w, method=METHOD_SURFACE):
+def pair_bin_areas(tx_row, xi, w, method=METHOD_SURFACE, lut=(1000, 1000)):
     """(b_min, areas per fine bin) of one voxel-transducer pair; method
-    METHOD_TRAPEZOID takes the trapezoidal arc integral for a cylinder."""
+    METHOD_TRAPEZOID takes the trapezoidal arc integral for a cylinder,
+    METHOD_LUT the elliptic closed form with E from lut = (N_s, N_m) tables."""
     tp, ip = time_args(w)
+    q1, q2 = (int(lut[0]), int(lut[1])) if method == METHOD_LUT else (0, 0)
     tx_row = np.ascontiguousarray(tx_row, dtype=np.float64)
     xi = np.ascontiguousarray(xi, dtype=np.float64)
     cap = 1 << 16
     out = np.zeros(cap)
     bmin = C.c_int64(0)
-    nb = lib().oracle_pair_bin_areas_m(tx_row, xi, tp, ip, int(method), C.byref(bmin), out, cap)
+    nb = lib().oracle_pair_bin_areas_m(tx_row, xi, tp, ip, int(method), q1, q2, C.byref(bmin), out, cap)
     if nb < 0:
         cap = -nb
         out = np.zeros(cap)
-        nb = lib().oracle_pair_bin_areas_m(tx_row, xi, tp, ip, int(method), C.byref(bmin), out, cap)
+        nb = lib().oracle_pair_bin_areas_m(tx_row, xi, tp, ip, int(method), q1, q2, C.byref(bmin), out, cap)
     return int(bmin.value), out[:nb].copy()
 
 
@@ -233,6 +240,16 @@ def ellip_f(phi, m):
 
 def ellip_e_any(theta, nu):
     return lib().oracle_ellip_e_any(theta, nu)
+
+
+def ellip_e_lut(theta, nu, ns=1000, nm=1000):
+    """E(theta, nu) from the ns x nm lookup tables (Sec. 4.2.2), any nu >= 0."""
+    return lib().oracle_ellip_e_lut(float(theta), float(nu), int(ns), int(nm))
+
+
+def lut_node(n, N):
+    """Node n (0-based) of the power-law grid of Eq. (LUT_sampling)."""
+    return lib().oracle_lut_node(int(n), int(N))
 
 
 # --------------------------------------------------------------------------

@@ -25,6 +25,11 @@
  *   - the trapezoidal arc integral (Eq. trapezoid_Il): exact on the focal
  *     line (flat level curves), exact group totals, convergence to the exact
  *     areas as the strip narrows, its own dot-product test;
+ *   - the lookup tables of E and F (Sec. 4.2.2): interpolated values against
+ *     scipy's incomplete integrals within the bilinear error bound, second
+ *     order in the grid step, the reciprocal-modulus branch against direct
+ *     quadrature of the integrand, exact group totals, operator convergence
+ *     to the exact areas as the tables grow, its own dot-product test;
  *   - the whole chain against the continuous model (Prop. 1 + Eq. 3,4) at
  *     growing U (Prop. 3), the point method against the surface method at
  *     growing Q (Prop. 2), translation/rotation invariance and the
@@ -43,6 +48,7 @@
 #define OR_METHOD_SURFACE 0
 #define OR_METHOD_POINT 1
 #define OR_METHOD_TRAPEZOID 2 /* surface method, Eq. (trapezoid_Il) for the cylinder arc integral */
+#define OR_METHOD_LUT 3       /* surface method, Eq. (cyl_Il) with E from the lookup tables of Sec. 4.2.2 */
 
 /* Transducer descriptor: 16 doubles
  *   [0] kind, [1..3] c0, [4..6] e1, [7..9] e2,
@@ -291,9 +297,111 @@ static double phi_hat(const opair *p, const oquad *q, double v, double r)
     return acos(arg);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Lookup tables (Sec. 4.2.2): E~(s, m) = E(arcsin s, m) and                 */
+/* F~(s, m) = F(arcsin s, m) on the power-law grid of Eq. (LUT_sampling),    */
+/* g_n = (1 - eps) [1 - (1 - n / (N - 1))^4], n = 0 .. N - 1 (0-based), for  */
+/* both s and m, eps = 1e-16; a query is interpolated bilinearly in the cell */
+/* that holds it.  The tables of one (N_s, N_m) are built once, from the     */
+/* Carlson forms above, and kept.                                            */
+/* ------------------------------------------------------------------------ */
+#define OR_LUT_EPS 1e-16
+
+typedef struct {
+    int ns, nm;
+    double *gs, *gm; /* grid nodes of s and m */
+    double *E, *F;   /* [ns][nm] */
+} olut;
+
+static olut g_lut = {0, 0, NULL, NULL, NULL, NULL};
+
+static double lut_node(int n, int N)
+{
+    double x = 1.0 - (double)n / (double)(N - 1);
+    return (1.0 - OR_LUT_EPS) * (1.0 - x * x * x * x);
+}
+
+/* Not thread-safe: called before any parallel region. */
+static const olut *lut_get(int ns, int nm)
+{
+    if (ns < 2 || nm < 2) return NULL;
+    if (g_lut.ns == ns && g_lut.nm == nm) return &g_lut;
+    free(g_lut.gs);
+    free(g_lut.gm);
+    free(g_lut.E);
+    free(g_lut.F);
+    g_lut.ns = ns;
+    g_lut.nm = nm;
+    g_lut.gs = (double *)malloc(sizeof(double) * (size_t)ns);
+    g_lut.gm = (double *)malloc(sizeof(double) * (size_t)nm);
+    g_lut.E = (double *)malloc(sizeof(double) * (size_t)ns * (size_t)nm);
+    g_lut.F = (double *)malloc(sizeof(double) * (size_t)ns * (size_t)nm);
+    for (int i = 0; i < ns; ++i) g_lut.gs[i] = lut_node(i, ns);
+    for (int j = 0; j < nm; ++j) g_lut.gm[j] = lut_node(j, nm);
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int i = 0; i < ns; ++i) {
+        double phi = asin(g_lut.gs[i]);
+        for (int j = 0; j < nm; ++j) {
+            g_lut.E[(size_t)i * nm + j] = ellip_e(phi, g_lut.gm[j]);
+            g_lut.F[(size_t)i * nm + j] = ellip_f(phi, g_lut.gm[j]);
+        }
+    }
+    return &g_lut;
+}
+
+/* Cell c with g[c] <= z <= g[c+1] (z clamped into [g_0, g_{N-1}]), from the
+ * inverse of Eq. (LUT_sampling), n = (N - 1) [1 - (1 - z / (1 - eps))^(1/4)]
+ * (two square roots), then moved by whole cells until it holds z; *w is the
+ * position of z in the cell. */
+static int lut_cell(const double *g, int N, double z, double *w)
+{
+    if (z < 0.0) z = 0.0;
+    if (z > g[N - 1]) z = g[N - 1];
+    double y = 1.0 - z / (1.0 - OR_LUT_EPS);
+    double x = 1.0 - sqrt(sqrt(y > 0.0 ? y : 0.0));
+    int c = (int)floor(x * (double)(N - 1));
+    if (c < 0) c = 0;
+    if (c > N - 2) c = N - 2;
+    while (c < N - 2 && z > g[c + 1]) ++c;
+    while (c > 0 && z < g[c]) --c;
+    *w = (z - g[c]) / (g[c + 1] - g[c]);
+    return c;
+}
+
+static double lut_bilinear(const olut *t, const double *T, double s, double m)
+{
+    double ws, wm;
+    int i = lut_cell(t->gs, t->ns, s, &ws);
+    int j = lut_cell(t->gm, t->nm, m, &wm);
+    const double *r0 = T + (size_t)i * t->nm + j, *r1 = r0 + t->nm;
+    return (1.0 - ws) * ((1.0 - wm) * r0[0] + wm * r0[1]) + ws * ((1.0 - wm) * r1[0] + wm * r1[1]);
+}
+
+/* E(theta, nu) from the tables: E~(sin theta, nu) for nu <= 1; for nu > 1 the
+ * reciprocal-modulus transformation of Eq. (reciprocal_modulus) with
+ * sin(theta~) = sqrt(nu) sin(theta), on E~ and F~ at parameter 1 / nu. */
+static double ellip_e_lut(const olut *t, double theta, double nu)
+{
+    if (nu <= 1.0) return lut_bilinear(t, t->E, sin(theta), nu);
+    double sn = sqrt(nu) * sin(theta);
+    if (sn > 1.0) sn = 1.0; /* Lemma 6 keeps it <= 1; rounding may not */
+    double m = 1.0 / nu;
+    return sqrt(nu) * (lut_bilinear(t, t->E, sn, m) - (1.0 - m) * lut_bilinear(t, t->F, sn, m));
+}
+
+double oracle_ellip_e_lut(double theta, double nu, int ns, int nm)
+{
+    const olut *t = lut_get(ns, nm);
+    return t ? ellip_e_lut(t, theta, nu) : NAN;
+}
+
+double oracle_lut_node(int n, int N) { return lut_node(n, N); }
+
 /* I(r) = integral of Psi(u, r) over [alpha, beta]: Eq. (plane_primitive) for
- * the plane, Eq. (cyl_Il) with Lemma 6 for the cylinder. */
-static double arc_integral(const opair *p, double alpha, double beta, double r)
+ * the plane, Eq. (cyl_Il) with Lemma 6 for the cylinder, E exact or (lut not
+ * NULL) from the lookup tables.  On the focal line (rho = 0) E(theta, 0) =
+ * theta and I is (beta - alpha) sqrt(q) in both cases. */
+static double arc_integral(const opair *p, double alpha, double beta, double r, const olut *lut)
 {
     if (!(beta > alpha)) return 0.0;
     if (p->kind == OR_PLANE) {
@@ -318,6 +426,7 @@ static double arc_integral(const opair *p, double alpha, double beta, double r)
     if (q <= 0.0) return 0.0; /* Lemma 6: degenerate, integral vanishes */
     if (rho == 0.0) return (beta - alpha) * sqrt(q);
     double nu = 4.0 * R * rho / q;
+    if (lut) return 2.0 * sqrt(q) * (ellip_e_lut(lut, 0.5 * beta, nu) - ellip_e_lut(lut, 0.5 * alpha, nu));
     return 2.0 * sqrt(q) * (ellip_e_any(0.5 * beta, nu) - ellip_e_any(0.5 * alpha, nu));
 }
 
@@ -328,7 +437,7 @@ static double arc_integral(const opair *p, double alpha, double beta, double r)
 static double arc_integral_trapezoid(const opair *p, double alpha, double beta, double r)
 {
     if (!(beta > alpha)) return 0.0;
-    if (p->kind == OR_PLANE) return arc_integral(p, alpha, beta, r);
+    if (p->kind == OR_PLANE) return arc_integral(p, alpha, beta, r, NULL);
     double ha = r * r - psi_of(p, alpha), hb = r * r - psi_of(p, beta);
     return 0.5 * (beta - alpha) * (sqrt(ha > 0.0 ? ha : 0.0) + sqrt(hb > 0.0 ? hb : 0.0));
 }
@@ -336,9 +445,11 @@ static double arc_integral_trapezoid(const opair *p, double alpha, double beta, 
 /* Group areas of one pair (Alg. 4 with the coarser area grid of Remark 1).
  * Bins [b_min, b_max] from Eq. (rmin_rmax); group j covers the fine bins
  * [b_min + j dl, min(b_min + (j+1) dl, b_max + 1)).  Returns the number of
- * groups written into areas[] (grown on demand).  trap: the trapezoidal I_l. */
+ * groups written into areas[] (grown on demand).  method: the I_l of
+ * OR_METHOD_SURFACE (exact), OR_METHOD_TRAPEZOID or OR_METHOD_LUT (tables
+ * lut). */
 static int pair_group_areas(const opair *p, const otime *tm, int64_t *bmin_out, int64_t *bmax_out,
-                            double **areas, int *cap, int trap)
+                            double **areas, int *cap, int method, const olut *lut)
 {
     const double ufs = (double)tm->U * tm->fs;
     int64_t bmin = (int64_t)floor((p->rmin / tm->c - tm->t0) * ufs);
@@ -370,7 +481,8 @@ static int pair_group_areas(const opair *p, const otime *tm, int64_t *bmin_out, 
             const oquad *q = &p->q[i];
             double a = phi_hat(p, q, q->vmax, r); /* Eq. (alphabeta) */
             double bb = phi_hat(p, q, q->vmin, r);
-            double I = trap ? arc_integral_trapezoid(p, a, bb, r) : arc_integral(p, a, bb, r);
+            double I = method == OR_METHOD_TRAPEZOID ? arc_integral_trapezoid(p, a, bb, r)
+                       : arc_integral(p, a, bb, r, method == OR_METHOD_LUT ? lut : NULL);
             /* Eq. (area_D_l_xi) and Eq. (swept_u) */
             area += p->J0 * ((a - al[i]) * q->vmax + I - Il[i] - (bb - be[i]) * q->vmin);
             al[i] = a;
@@ -397,7 +509,7 @@ static void voxel_pos(const int *n, const double *origin, double pitch, int64_t 
  * cap entries; returns the number of fine bins or -needed when too small.
  * method: OR_METHOD_SURFACE, or OR_METHOD_TRAPEZOID for Eq. (trapezoid_Il). */
 int64_t oracle_pair_bin_areas_m(const double *tx, const double *x, const double *tp, const int *ip, int method,
-                                int64_t *b_min, double *out_area, int64_t cap)
+                                int q1, int q2, int64_t *b_min, double *out_area, int64_t cap)
 {
     otime tm = mk_time(tp, ip);
     opair p;
@@ -405,7 +517,8 @@ int64_t oracle_pair_bin_areas_m(const double *tx, const double *x, const double 
     double *areas = NULL;
     int acap = 0;
     int64_t bmin, bmax;
-    int ng = pair_group_areas(&p, &tm, &bmin, &bmax, &areas, &acap, method == OR_METHOD_TRAPEZOID);
+    const olut *lut = method == OR_METHOD_LUT ? lut_get(q1, q2) : NULL;
+    int ng = pair_group_areas(&p, &tm, &bmin, &bmax, &areas, &acap, method, lut);
     int64_t nb = bmax - bmin + 1;
     *b_min = bmin;
     if (nb > cap) {
@@ -424,7 +537,7 @@ int64_t oracle_pair_bin_areas_m(const double *tx, const double *x, const double 
 int64_t oracle_pair_bin_areas(const double *tx, const double *x, const double *tp, const int *ip,
                               int64_t *b_min, double *out_area, int64_t cap)
 {
-    return oracle_pair_bin_areas_m(tx, x, tp, ip, OR_METHOD_SURFACE, b_min, out_area, cap);
+    return oracle_pair_bin_areas_m(tx, x, tp, ip, OR_METHOD_SURFACE, 0, 0, b_min, out_area, cap);
 }
 
 /* Exported: r_min, r_max of Eq. (rmin_rmax) and the quadrant count. */
@@ -475,6 +588,7 @@ int64_t oracle_geometric_forward(const int *n, const double *origin, double pitc
     const int64_t UL = (int64_t)tm.U * tm.L;
     const double ufs = (double)tm.U * tm.fs;
     int64_t dropped = 0;
+    const olut *lut = method == OR_METHOD_LUT ? lut_get(q1, q2) : NULL; /* q1 x q2 = N_s x N_m */
     if (!vox_idx) n_vox = (int64_t)n[0] * n[1] * n[2];
     memset(f, 0, sizeof(double) * (size_t)UL * (size_t)K);
     for (int k = 0; k < K; ++k) {
@@ -512,7 +626,7 @@ int64_t oracle_geometric_forward(const int *n, const double *origin, double pitc
                     opair p;
                     pair_setup(t, xi, &p);
                     int64_t bmin, bmax;
-                    int ng = pair_group_areas(&p, &tm, &bmin, &bmax, &areas, &acap, method == OR_METHOD_TRAPEZOID);
+                    int ng = pair_group_areas(&p, &tm, &bmin, &bmax, &areas, &acap, method, lut);
                     for (int j = 0; j < ng; ++j) {
                         int64_t e0 = bmin + (int64_t)j * tm.dl, e1 = e0 + tm.dl;
                         if (e1 > bmax + 1) e1 = bmax + 1;
@@ -546,6 +660,7 @@ int64_t oracle_geometric_adjoint(const int *n, const double *origin, double pitc
     const int64_t UL = (int64_t)tm.U * tm.L;
     const double ufs = (double)tm.U * tm.fs;
     int64_t dropped = 0;
+    const olut *lut = method == OR_METHOD_LUT ? lut_get(q1, q2) : NULL; /* q1 x q2 = N_s x N_m */
     if (!vox_idx) n_vox = (int64_t)n[0] * n[1] * n[2];
 #pragma omp parallel reduction(+ : dropped)
     {
@@ -580,7 +695,7 @@ int64_t oracle_geometric_adjoint(const int *n, const double *origin, double pitc
                     opair p;
                     pair_setup(t, xi, &p);
                     int64_t bmin, bmax;
-                    int ng = pair_group_areas(&p, &tm, &bmin, &bmax, &areas, &acap, method == OR_METHOD_TRAPEZOID);
+                    int ng = pair_group_areas(&p, &tm, &bmin, &bmax, &areas, &acap, method, lut);
                     for (int j = 0; j < ng; ++j) {
                         int64_t e0 = bmin + (int64_t)j * tm.dl, e1 = e0 + tm.dl;
                         if (e1 > bmax + 1) e1 = bmax + 1;
