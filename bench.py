@@ -364,8 +364,9 @@ def c5_line(api, dev, n_pos):
 def exp1_line(api, dev):
     """The paper's Experiment 1 system (fine grid: 98,415 voxels x 215
     cylindrical elements, 2688 samples at 62.5 MHz): one A plus one A^T with
-    the exact areas, the trapezoidal approximation, Piecewise-Planes with 30
-    planes and the point method with 25 x 25 points (Q = 625), each with its
+    the exact areas, the paper's lookup tables (1000 x 1000), the trapezoidal
+    approximation, Piecewise-Planes with 30 planes and the point method with
+    25 x 25 points (Q = 625), each with its
     distance to the exact A x.  The paper's own per-iteration times (A100,
     FP64, one A and one A^T assumed per iteration) are context, not targets."""
     import torch
@@ -374,6 +375,7 @@ def exp1_line(api, dev):
     x = torch.from_numpy(w.x).to(dev)
     taps = api.system_taps(w, dev)
     ops = {"exact": api.Plan(w, taps=taps, device=dev),
+           "lut_1000x1000": api.Plan(w.with_(method=W.METHOD_LUT, q1=1000, q2=1000), taps=taps, device=dev),
            "trapezoidal": api.Plan(w.with_(method=W.METHOD_TRAPEZOID), taps=taps, device=dev),
            "piecewise_planes_30": api.Plan(w, taps=taps, piecewise_planes=30, device=dev),
            "point_625": api.Plan(w.with_(method=W.METHOD_POINT, q1=25, q2=25), taps=taps, device=dev)}

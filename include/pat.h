@@ -48,8 +48,16 @@ enum { PAT_PLANE = 0, PAT_CYLINDER = 1 };
 /* PAT_METHOD_TRAPEZOID: the surface method with the paper's trapezoidal
  * approximation of the cylinder's arc integral (Eq. trapezoid_Il: the level
  * curve between its two ends replaced by its chord); planes keep their
- * closed form.  An approximation of PAT_METHOD_SURFACE, cheaper per area. */
-enum { PAT_METHOD_SURFACE = 0, PAT_METHOD_POINT = 1, PAT_METHOD_TRAPEZOID = 2 };
+ * closed form.  An approximation of PAT_METHOD_SURFACE, cheaper per area.
+ * PAT_METHOD_LUT: the surface method with the cylinder's arc integral in the
+ * elliptic closed form of Eq. (cyl_Il), E read from the paper's lookup tables
+ * (Sec. 4.2.2): E~(s, m) = E(arcsin s, m) and F~(s, m) = F(arcsin s, m) on the
+ * power-law grid of Eq. (LUT_sampling) with eps = 1e-16, q1 nodes in s and q2
+ * in m, bilinear interpolation, the reciprocal-modulus transformation of
+ * Eq. (reciprocal_modulus) for nu > 1.  The tables (16 q1 q2 bytes of device
+ * memory, plus the node arrays) are built at plan creation; the arc integral
+ * is evaluated in FP64.  Planes keep their closed form. */
+enum { PAT_METHOD_SURFACE = 0, PAT_METHOD_POINT = 1, PAT_METHOD_TRAPEZOID = 2, PAT_METHOD_LUT = 3 };
 enum { PAT_RBF_BUMP = 0, PAT_RBF_CONE = 1, PAT_RBF_WENDLAND = 2 };
 enum { PAT_EIR_GAUSS_SINE = 0, PAT_EIR_BOX = 1 };
 /* Plan flags (pat_params.flags, OR-ed):
@@ -100,9 +108,10 @@ typedef struct pat_transducer {
  * dl the area step of Remark 1 (1 <= dl <= U; dl = 1 is Alg. 3 exactly).
  * Groups of dl fine bins start at each pair's first bin l_min of
  * Eq. (rmin_rmax); the last group stops at l_max and its area is split over
- * its actual length.  method: PAT_METHOD_SURFACE (Alg. 3 + Alg. 4) or
+ * its actual length.  method: PAT_METHOD_SURFACE (Alg. 3 + Alg. 4),
  * PAT_METHOD_POINT (Alg. 2 with a q1 x q2 midpoint quadrature of each
- * element, Prop. 2).  flags: PAT_FLAG_ALLOW_CLIP drops fine bins outside
+ * element, Prop. 2), PAT_METHOD_TRAPEZOID, or PAT_METHOD_LUT (q1 x q2 table
+ * nodes in s and m, each 2 .. 8192; the paper takes 1000 x 1000).  flags: PAT_FLAG_ALLOW_CLIP drops fine bins outside
  * [0, U L) instead of failing plan creation. */
 typedef struct pat_params {
     double c;  /* speed of sound, > 0 */

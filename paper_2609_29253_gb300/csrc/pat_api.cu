@@ -42,6 +42,8 @@ struct pat_plan {
     TcGeometry tcg;
     uint8_t *tc_fwd_tab, *tc_adj_tab;
     int *tc_err;
+    // PAT_METHOD_LUT: the tables of E~ and F~ with their node arrays (one allocation)
+    void *lut_buf;
     pat_plan_info info;
 };
 
@@ -122,10 +124,13 @@ static pat_status validate(const pat_grid *grid, const pat_transducer *tx, int K
     if (p->L < 1 || p->U < 1 || p->dl < 1 || p->dl > p->U)
         return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: need L >= 1, U >= 1, 1 <= dl <= U");
     if ((long long)p->L * p->U >= (1LL << 30)) return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: U L too large");
-    if (p->method != PAT_METHOD_SURFACE && p->method != PAT_METHOD_POINT && p->method != PAT_METHOD_TRAPEZOID)
+    if (p->method != PAT_METHOD_SURFACE && p->method != PAT_METHOD_POINT && p->method != PAT_METHOD_TRAPEZOID &&
+        p->method != PAT_METHOD_LUT)
         return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: unknown method %d", p->method);
     if (p->method == PAT_METHOD_POINT && (p->q1 < 1 || p->q2 < 1))
         return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: point method needs q1, q2 >= 1");
+    if (p->method == PAT_METHOD_LUT && (p->q1 < 2 || p->q2 < 2 || p->q1 > 8192 || p->q2 > 8192))
+        return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: lookup tables need 2 <= q1, q2 <= 8192 nodes");
     if (!(kappa > 0)) return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: kappa must be > 0");
     if (n_taps < 1) return fail(PAT_ERR_INVALID_ARG, "pat_plan_create: n_taps must be >= 1");
     if (p->flags & ~(PAT_FLAG_ALLOW_CLIP | PAT_FLAG_CONV_TC | PAT_FLAG_PIECEWISE_PLANES))
@@ -307,6 +312,30 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
             rc = fail(PAT_ERR_CUDA, "pat_plan_create: setup kernels failed");
             break;
         }
+        if (params->method == PAT_METHOD_LUT) {
+            const int ns = params->q1, nm = params->q2;
+            const size_t tb = sizeof(double2) * (size_t)ns * nm;
+            if (cudaMalloc(&p->lut_buf, tb + 2 * sizeof(double) * (size_t)(ns + nm)) != cudaSuccess) {
+                rc = fail(PAT_ERR_CUDA, "pat_plan_create: cudaMalloc of the lookup tables failed");
+                break;
+            }
+            LutDev &L = tm.lut;
+            double2 *T = (double2 *)p->lut_buf;
+            double *gs = (double *)(T + (size_t)ns * nm), *hs = gs + ns, *gm = hs + ns, *hm = gm + nm;
+            L.T = T;
+            L.gs = gs;
+            L.hs = hs;
+            L.gm = gm;
+            L.hm = hm;
+            L.ns = ns;
+            L.nm = nm;
+            L.top_s = lut_grid(ns - 1, ns);
+            L.top_m = lut_grid(nm - 1, nm);
+            if (launch_lut_tables(ns, nm, T, gs, hs, gm, hm, s) != cudaSuccess) {
+                rc = fail(PAT_ERR_CUDA, "pat_plan_create: lookup-table kernel failed");
+                break;
+            }
+        }
         if (p->tc) {
             if (cudaMalloc(&p->tc_fwd_tab, p->tcg.fwd_table_bytes) != cudaSuccess ||
                 cudaMalloc(&p->tc_adj_tab, p->tcg.adj_table_bytes) != cudaSuccess ||
@@ -447,6 +476,7 @@ extern "C" pat_status pat_plan_destroy(pat_plan *p)
     cudaFree(p->tc_fwd_tab);
     cudaFree(p->tc_adj_tab);
     cudaFree(p->tc_err);
+    cudaFree(p->lut_buf);
     cudaSetDevice(cur);
     delete p;
     return PAT_OK;

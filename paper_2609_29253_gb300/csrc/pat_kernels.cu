@@ -22,6 +22,12 @@
 
 namespace pat {
 
+// the arc-integral mode of a surface method
+__host__ __device__ constexpr int area_mode(int method)
+{
+    return method == PAT_METHOD_TRAPEZOID ? kAreaTrap : method == PAT_METHOD_LUT ? kAreaLut : kAreaExact;
+}
+
 // ---------------------------------------------------------------------------
 // frames
 // ---------------------------------------------------------------------------
@@ -69,6 +75,7 @@ __global__ void frames_kernel(const double *__restrict__ raw, int K, double ox, 
     t.Lzd = r[14];
     t.cthd = cos(r[13]);
     t.sthd = sin(r[13]);
+    t.thmaxd = r[13];
     t.L1 = (float)r[10];
     t.L2 = (float)r[11];
     t.R = (float)r[12];
@@ -271,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 3) fwd_geom_kernel(const TxDev *__re
                 point_pair<KIND>(t, tm, ix, iy, iz, s);
             } else {
                 FwdSurfaceSink s{win, xv, 0.f};
-                surface_pair<KIND, false, METHOD == PAT_METHOD_TRAPEZOID>(t, tm, ix, iy, iz, s, glx, glw);
+                surface_pair<KIND, false, area_mode(METHOD)>(t, tm, ix, iy, iz, s, glx, glw);
             }
         }
         __syncwarp();
@@ -601,7 +608,7 @@ __global__ void __launch_bounds__(kThreads, 3) adj_geom_kernel(const TxDev *__re
             } else {
                 AdjSurfaceSink s{(const float2 *)Pv + (size_t)rows[k] * stride, tm.UL, 0.f, make_float2(0.f, 0.f),
                                  false};
-                surface_pair<KIND, false, METHOD == PAT_METHOD_TRAPEZOID>(t, tm, ix, iy, iz, s, glx, glw);
+                surface_pair<KIND, false, area_mode(METHOD)>(t, tm, ix, iy, iz, s, glx, glw);
                 acc += (double)s.acc;
             }
         }
@@ -885,6 +892,11 @@ cudaError_t launch_fwd_geom(const TxDev *tx, int Kf, int K, const int *rows, int
             return fwd_geom_go<PAT_METHOD_TRAPEZOID, PAT_CYLINDER>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
         return fwd_geom_go<PAT_METHOD_TRAPEZOID, kKindAny>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
     }
+    if (tm.method == PAT_METHOD_LUT && kind != PAT_PLANE) { // planes keep their closed form
+        if (kind == PAT_CYLINDER)
+            return fwd_geom_go<PAT_METHOD_LUT, PAT_CYLINDER>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
+        return fwd_geom_go<PAT_METHOD_LUT, kKindAny>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
+    }
     if (kind == PAT_PLANE) return fwd_geom_go<PAT_METHOD_SURFACE, PAT_PLANE>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
     if (kind == PAT_CYLINDER)
         return fwd_geom_go<PAT_METHOD_SURFACE, PAT_CYLINDER>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
@@ -963,6 +975,10 @@ cudaError_t launch_adj_geom(const TxDev *tx, int K, const int *rows, int kind, c
         else if (kind == PAT_CYLINDER)
             adj_geom_kernel<PAT_METHOD_TRAPEZOID, PAT_CYLINDER><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z, rows);
         else adj_geom_kernel<PAT_METHOD_TRAPEZOID, kKindAny><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z, rows);
+    } else if (tm.method == PAT_METHOD_LUT && kind != PAT_PLANE) { // planes keep their closed form
+        if (kind == PAT_CYLINDER)
+            adj_geom_kernel<PAT_METHOD_LUT, PAT_CYLINDER><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z, rows);
+        else adj_geom_kernel<PAT_METHOD_LUT, kKindAny><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z, rows);
     } else {
         if (kind == PAT_PLANE) adj_geom_kernel<PAT_METHOD_SURFACE, PAT_PLANE><<<grid, thr, 0, st>>>(tx, K, tm, g, P, z, rows);
         else if (kind == PAT_CYLINDER)

@@ -48,5 +48,8 @@ cudaError_t launch_fista(float *y, const float *g, float *xo, long long n, float
                          cudaStream_t st);
 cudaError_t launch_dot(const float *a, const float *b, long long n, double *out, cudaStream_t st);
 cudaError_t launch_scale(const float *a, float *o, long long n, const double *nrm2, cudaStream_t st);
+// PAT_METHOD_LUT: T [ns][nm] (E~, F~), nodes gs, gm and reciprocal cell widths hs, hm (pat_lut.cu)
+cudaError_t launch_lut_tables(int ns, int nm, double2 *T, double *gs, double *hs, double *gm, double *hm,
+                              cudaStream_t st);
 
 } // namespace pat

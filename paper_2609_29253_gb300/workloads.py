@@ -44,6 +44,8 @@ CYLINDER = 1
 METHOD_SURFACE = 0
 METHOD_POINT = 1
 METHOD_TRAPEZOID = 2
+METHOD_LUT = 3  # surface method, cylinder arc integral from the paper's E / F lookup tables (q1 x q2 nodes)
+LUT_PAPER = (1000, 1000)  # the paper's table sizes N_s x N_nu
 RBF_BUMP = 0  # (1 - r^2/k^2)^2
 RBF_CONE = 1  # 1 - r/k
 RBF_WENDLAND = 2  # (1 - r/k)^2
@@ -311,6 +313,12 @@ def _make(name, n, pitch, tx, c, fs, t0, L, U, kappa, eir, x=None, dl=None, rbf=
                     method=method, q1=int(q[0]), q2=int(q[1]), x=x, meta=dict(meta or {}))
 
 
+def method_q(method, q, lut=LUT_PAPER):
+    """(q1, q2) of a workload: the point method's quadrature, the LUT's table
+    sizes, else (0, 0)."""
+    return tuple(q) if method == METHOD_POINT else tuple(lut) if method == METHOD_LUT else (0, 0)
+
+
 def c1(dl=None, method=METHOD_SURFACE, q=(64, 64), seed=0):
     """16^3 voxels, 32 planar 1x1 mm elements on a 10 mm Fibonacci sphere."""
     n = (16, 16, 16)
@@ -318,7 +326,7 @@ def c1(dl=None, method=METHOD_SURFACE, q=(64, 64), seed=0):
     tx = fibonacci_planar(32, 10e-3, 0.5e-3, 0.5e-3)
     x = uniform_phantom(16 ** 3, seed)
     return _make("c1: 16^3 @ 0.1 mm, 32 planar 1x1 mm, L=256 @ 40 MHz", n, pitch, tx, 1500.0, 40e6, 5.0e-6, 256, 11,
-                 1.5 * pitch, gauss_sine_eir(5e6), x=x, dl=dl, method=method, q=q if method == METHOD_POINT else (0, 0))
+                 1.5 * pitch, gauss_sine_eir(5e6), x=x, dl=dl, method=method, q=method_q(method, q))
 
 
 C2_ARRAY = dict(n_el=128, el_pitch=0.3e-3, R=20e-3, theta_max=math.asin(0.25), Lz=0.15e-3)
@@ -386,7 +394,7 @@ def c4_problem(p, n_range=(48, 160), k_range=(1024, 8192), seed_base=1000):
                  1500.0, 40e6, t0, L, 11, 1.5 * pitch, gauss_sine_eir(5e6), x=x)
 
 
-def exp1(grid="fine", method=METHOD_SURFACE, q=(25, 25)):
+def exp1(grid="fine", method=METHOD_SURFACE, q=(25, 25), lut=LUT_PAPER):
     """The paper's controlled synthetic study (Sec. 5.2): 215 cylindrically
     focused elements (R 25 mm, 7.5 mm elevation aperture, 0.25 mm wide)
     rotated about their focal line at 43 azimuths, at 5 positions spanning
@@ -405,7 +413,7 @@ def exp1(grid="fine", method=METHOD_SURFACE, q=(25, 25)):
     x = rod_phantom(n, origin, pitch)
     return _make(f"exp1 ({grid}): {n[0]}x{n[1]}x{n[2]} @ {pitch * 1e6:.0f} um, 215 cylindrical elements, "
                  f"L=2688 @ 62.5 MHz", n, pitch, np.array(rows), 1500.0, 62.5e6, 0.0, 2688, 11, 1.5 * pitch,
-                 gauss_sine_eir(5e6, frac_bw=1.6), x=x, method=method, q=q if method == METHOD_POINT else (0, 0))
+                 gauss_sine_eir(5e6, frac_bw=1.6), x=x, method=method, q=method_q(method, q, lut))
 
 
 def small_cylinder(n_vox=12, n_angles=4, n_el=4, seed=0, dl=None, L=None):

@@ -105,6 +105,49 @@ def test_cylinder_trapezoid(api, orc, dl):
     assert 0.0 < rel(s_ref, s_ex) < 0.2
 
 
+@pytest.mark.parametrize("dl,lut", [(1, (1000, 1000)), (11, (1000, 1000)), (11, (181, 263))])
+def test_cylinder_lut(api, orc, dl, lut):
+    """The paper's lookup tables (Sec. 4.2.2) against the oracle's own LUT
+    areas, all stages: the paper's 1000 x 1000 tables, and small non-square
+    ones (other cells, other index inversions); and the distance of the LUT
+    operator to the exact one."""
+    w = W.small_cylinder(n_vox=12, n_angles=4, n_el=3, dl=dl).with_(method=W.METHOD_LUT, q1=lut[0], q2=lut[1])
+    _, s, s_ref = _run(api, orc, w)
+    s_ex, _ = orc.forward(w.with_(method=W.METHOD_SURFACE, q1=0, q2=0), orc.taps_for(w),
+                          w.x.astype(np.float32).astype(np.float64))
+    assert 0.0 < rel(s_ref, s_ex) < 0.05
+
+
+def _axis_rows(n_az=4, zc=(-1.3e-3, 0.0, 2.1e-3)):
+    """Cylinders focused on the z axis (focal line = z axis), frames built from
+    exact unit vectors, so that voxels on the axis have rho = 0 exactly."""
+    a = W.C2_ARRAY
+    e2s = [np.array(v, dtype=float) for v in ((1, 0, 0), (0, 1, 0), (-1, 0, 0), (0, -1, 0))][:n_az]
+    return np.array([W.cylinder_row(np.array([0.0, 0.0, z]), np.array([0.0, 0.0, 1.0]), e2, a["R"], a["theta_max"],
+                                    a["Lz"]) for z in zc for e2 in e2s])
+
+
+def test_lut_on_the_focal_line(api, orc):
+    """Voxels exactly on the focal line (rho = 0: E is never read) and next to
+    it, LUT against the oracle's LUT."""
+    n, pitch = 7, 2.0 ** -13  # exact pitch: the centre column lies on the axis in FP64 and in float-float
+    w = W.small_cylinder(n_vox=n).with_tx(_axis_rows())
+    w = w.with_(pitch=pitch, origin=W.centred_origin((n, n, n), pitch), t0=5.00037e-6, L=2048,
+                method=W.METHOD_LUT, q1=1000, q2=1000)
+    _run(api, orc, w, check_stages=False)
+
+
+def test_lut_c2_geometry_reduced(api, orc):
+    """The c2 element and rotation geometry on a coarse grid, LUT operator."""
+    n = 16
+    pitch = 12.8e-3 / n
+    w = W.c2(angles=np.array([0.3, 1.7]), with_x=False)
+    w = w.with_tx(w.tx[np.arange(0, 256, 8)]).with_(n=(n, n, n), pitch=pitch, origin=W.centred_origin((n, n, n), pitch))
+    w = w.with_(x=W.blob_phantom(w.n, w.origin, pitch, 30, 1, sigma=(0.4e-3, 1.2e-3)), method=W.METHOD_LUT, q1=1000,
+                q2=1000)
+    _run(api, orc, w, check_stages=False)
+
+
 @pytest.mark.parametrize("n_planes", [1, 8, 30])
 def test_cylinder_piecewise_planes(api, orc, n_planes):
     """Piecewise-Planes (Sec. 4.3): the library's own tangent-plane expansion
