@@ -65,6 +65,8 @@ def parse():
                    help="voxels per axis over the same 12.8 mm cube (128 = the c2 grid; smaller for profiling)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the convolution, batched-FISTA and c3 comparisons after the main timing")
+    p.add_argument("--extras", default="conv,fista,c3,c5,exp1",
+                   help="comma-separated extra lines to run: conv, fista, c3, c5, exp1")
     p.add_argument("--fista-problems", type=int, default=8)
     p.add_argument("--fista-iters", type=int, default=10)
     p.add_argument("--c3-positions", type=int, default=128)
@@ -479,6 +481,11 @@ def main():
     sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
     peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the clock seen
     ach = flops / mean_adj / 1e12
+    # the same denominators measured by the library's own dependent-chain kernels (after the timed region)
+    mp = _lib.pat_measure_peaks()
+    measured = {"fp32_ffma_tflops": mp["fp32_ffma_flops"] / 1e12, "fp32_ffma2_tflops": mp["fp32_ffma2_flops"] / 1e12,
+                "fp64_dfma_tflops": mp["fp64_dfma_flops"] / 1e12, "sfu_rsqrt_tops": mp["sfu_rsqrt_ops"] / 1e12,
+                "frac_of_measured_ffma": ach / (mp["fp32_ffma_flops"] / 1e12)}
 
     e2e = None
     if not args.no_e2e:
@@ -517,14 +524,20 @@ def main():
                "sample": f"{nv} seeded voxels x {wcpu.K} positions, A then A^T, FP64 ({dt:.1f} s)"}
 
     extras = {}
+    want = set(e.strip() for e in args.extras.split(",") if e.strip())
     if rank == 0 and not args.no_extras:
-        extras["conv_tcgen05"] = conv_compare(api, plans[args.warmup], c2w(args, angle_sets[args.warmup], with_x=False)
-                                              .with_(x=w0.x), taps, x, dev)
-        extras["fista_batched"] = fista_compare(api, dev, args.fista_problems, args.fista_iters)
-        extras["c3_precision_split"] = c3_line(api, dev, args.c3_positions)
-        if args.c5_positions > 0:
+        if "conv" in want:
+            extras["conv_tcgen05"] = conv_compare(api, plans[args.warmup],
+                                                  c2w(args, angle_sets[args.warmup], with_x=False).with_(x=w0.x), taps,
+                                                  x, dev)
+        if "fista" in want:
+            extras["fista_batched"] = fista_compare(api, dev, args.fista_problems, args.fista_iters)
+        if "c3" in want:
+            extras["c3_precision_split"] = c3_line(api, dev, args.c3_positions)
+        if "c5" in want and args.c5_positions > 0:
             extras["c5_full_scale_subset"] = c5_line(api, dev, args.c5_positions)
-        extras["exp1_operators"] = exp1_line(api, dev)
+        if "exp1" in want:
+            extras["exp1_operators"] = exp1_line(api, dev)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
@@ -537,7 +550,8 @@ def main():
                              "traffic": ADJ_TRAFFIC_BYTES if (args.grid == 128 and args.batch_angles == 4) else None,
                              "kernel": "adj_geom_kernel", "flops_per_unit": FLOPS_PER_QUAD_EVAL,
                              "units_per_launch": qe, "unit_name": "quadrant-edge area evaluation",
-                             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load"},
+                             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load",
+                             "measured_peaks": measured},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 4 * args.steps,
                 "clocks": clk, "wall_s_timed": t_wall}
         line.update(extras)

@@ -289,6 +289,20 @@ pat_status pat_plan_autotune(pat_plan *plan, const float *x, void *ws, size_t ws
 #define PAT_STATIC_SCRATCH_BYTES (16u << 20)
 pat_status pat_forward_static(pat_plan *plan, const float *x, float *s, void *stream);
 
+/* Arithmetic peaks of the current device, measured by dependent-chain
+ * kernels (8 independent chains per thread, 8 CTAs of 256 threads per SM,
+ * one warm-up launch then one timed launch each, about 10 ms per figure),
+ * in operations per second: FP32 fused multiply-add (2 flops each), the same
+ * on packed register pairs (__ffma2_rn, 4 flops per instruction), FP64 fused
+ * multiply-add, and rsqrtf on the special-function unit (1 op each).  The
+ * figures are those of the clocks at the time of the call.  Runs on `stream`
+ * and synchronises with it; allocates and frees a small device buffer.
+ * PAT_ERR_INVALID_ARG for a null out, PAT_ERR_CUDA on any CUDA failure. */
+typedef struct pat_peaks {
+    double fp32_ffma_flops, fp32_ffma2_flops, fp64_dfma_flops, sfu_rsqrt_ops;
+} pat_peaks;
+pat_status pat_measure_peaks(pat_peaks *out, void *stream);
+
 /* Thread-local description of the last failure ("" if none). */
 const char *pat_last_error(void);
 

@@ -45,6 +45,10 @@ class pat_system(C.Structure):
     _fields_ = [("rbf_kind", C.c_int32), ("eir_kind", C.c_int32), ("kappa", C.c_double), ("eir", C.c_double * 4)]
 
 
+class pat_peaks(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("fp32_ffma_flops", "fp32_ffma2_flops", "fp64_dfma_flops", "sfu_rsqrt_ops")]
+
+
 class pat_plan_info(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("N", "K", "L", "U", "UL", "dl", "method", "n_taps", "n_lo", "bin_lo",
                                          "bin_hi", "area_evals", "pair_bins", "quad_evals", "clipped_pairs",
@@ -56,7 +60,7 @@ class pat_plan_info(C.Structure):
 EXPORTS = ["pat_system_kernel", "pat_system_kernel_dc", "pat_plan_create", "pat_plan_destroy", "pat_plan_get_info",
            "pat_workspace_bytes", "pat_forward", "pat_adjoint", "pat_forward_geometric", "pat_conv_forward",
            "pat_conv_adjoint", "pat_adjoint_geometric", "pat_forward_dc", "pat_recon", "pat_recon_batch",
-           "pat_plan_autotune", "pat_forward_static", "pat_last_error", "pat_version"]
+           "pat_plan_autotune", "pat_forward_static", "pat_measure_peaks", "pat_last_error", "pat_version"]
 
 _lock = threading.Lock()
 _lib = None
@@ -107,6 +111,8 @@ def load(build_if_missing: bool = True):
         L.pat_recon_batch.argtypes = [vp, C.c_int32, vp, vp, C.c_int32, vp, vp, vp, vp, vp]
         L.pat_plan_autotune.restype = st
         L.pat_plan_autotune.argtypes = [vp, vp, vp, C.c_size_t, vp]
+        L.pat_measure_peaks.restype = st
+        L.pat_measure_peaks.argtypes = [C.POINTER(pat_peaks), vp]
         L.pat_last_error.restype = C.c_char_p
         L.pat_last_error.argtypes = []
         L.pat_version.restype = C.c_int32
@@ -227,6 +233,14 @@ def pat_plan_autotune(plan, x, ws, stream=None):
 
 def pat_forward_static(plan, x, s, stream=None):
     check(load().pat_forward_static(plan, _ptr(x), _ptr(s), _stream(stream)))
+
+
+def pat_measure_peaks(stream=None):
+    """Measured FP32 (FFMA, FFMA2), FP64 (DFMA) flop/s and SFU rsqrt op/s of
+    the current device (dependent-chain kernels)."""
+    out = pat_peaks()
+    check(load().pat_measure_peaks(C.byref(out), _stream(stream)))
+    return {f: getattr(out, f) for f, _ in pat_peaks._fields_}
 
 
 def pat_version():

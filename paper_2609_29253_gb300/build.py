@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpat.so")
-SOURCES = ["pat_kernels.cu", "pat_conv_tc.cu", "pat_lut.cu", "pat_api.cu"]
+SOURCES = ["pat_kernels.cu", "pat_conv_tc.cu", "pat_lut.cu", "pat_peaks.cu", "pat_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -57,6 +57,12 @@ def test_host_side_validation_without_gpu():
     assert L.pat_plan_create(C.byref(out), C.byref(g), tx, 1, C.byref(p), 1e-4, taps, 4, -1, None) == 1
     assert b"orthonormal" in L.pat_last_error()
     assert out.value is None
+    # lookup tables need 2 .. 8192 nodes per axis
+    p.method, p.q1, p.q2 = 3, 1, 1000
+    assert L.pat_plan_create(C.byref(out), C.byref(g), tx, 1, C.byref(p), 1e-4, taps, 4, -1, None) == 1
+    assert b"lookup tables" in L.pat_last_error()
+    assert out.value is None
+    assert L.pat_measure_peaks(None, None) == 1
 
 
 def test_build_flags_target_sm103a():
