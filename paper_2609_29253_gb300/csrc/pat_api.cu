@@ -281,9 +281,11 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
 
     // device constants
     double *raw = nullptr, *dorig = nullptr;
+    void *lut_scratch = nullptr; // FP64 node values of the lookup tables, freed once the cells are built
     auto cleanup = [&]() {
         cudaFree(raw);
         cudaFree(dorig);
+        cudaFree(lut_scratch);
     };
     if (cudaMalloc(&raw, sizeof(double) * 16 * (size_t)Kf) != cudaSuccess ||
         cudaMalloc(&p->tx, sizeof(TxDev) * (size_t)Kf) != cudaSuccess ||
@@ -314,25 +316,13 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
         }
         if (params->method == PAT_METHOD_LUT) {
             const int ns = params->q1, nm = params->q2;
-            const size_t tb = sizeof(double2) * (size_t)ns * nm;
-            if (cudaMalloc(&p->lut_buf, tb + 2 * sizeof(double) * (size_t)(ns + nm)) != cudaSuccess) {
+            if (cudaMalloc(&p->lut_buf, lut_bytes(ns, nm)) != cudaSuccess ||
+                cudaMalloc(&lut_scratch, sizeof(double2) * (size_t)ns * nm) != cudaSuccess) {
                 rc = fail(PAT_ERR_CUDA, "pat_plan_create: cudaMalloc of the lookup tables failed");
                 break;
             }
-            LutDev &L = tm.lut;
-            double2 *T = (double2 *)p->lut_buf;
-            double *gs = (double *)(T + (size_t)ns * nm), *hs = gs + ns, *gm = hs + ns, *hm = gm + nm;
-            L.T = T;
-            L.gs = gs;
-            L.hs = hs;
-            L.gm = gm;
-            L.hm = hm;
-            L.ns = ns;
-            L.nm = nm;
-            L.top_s = lut_grid(ns - 1, ns);
-            L.top_m = lut_grid(nm - 1, nm);
-            if (launch_lut_tables(ns, nm, T, gs, hs, gm, hm, s) != cudaSuccess) {
-                rc = fail(PAT_ERR_CUDA, "pat_plan_create: lookup-table kernel failed");
+            if (launch_lut_tables(ns, nm, p->lut_buf, (double2 *)lut_scratch, tm.lut, s) != cudaSuccess) {
+                rc = fail(PAT_ERR_CUDA, "pat_plan_create: lookup-table kernels failed");
                 break;
             }
         }

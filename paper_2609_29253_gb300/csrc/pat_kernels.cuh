@@ -48,8 +48,9 @@ cudaError_t launch_fista(float *y, const float *g, float *xo, long long n, float
                          cudaStream_t st);
 cudaError_t launch_dot(const float *a, const float *b, long long n, double *out, cudaStream_t st);
 cudaError_t launch_scale(const float *a, float *o, long long n, const double *nrm2, cudaStream_t st);
-// PAT_METHOD_LUT: T [ns][nm] (E~, F~), nodes gs, gm and reciprocal cell widths hs, hm (pat_lut.cu)
-cudaError_t launch_lut_tables(int ns, int nm, double2 *T, double *gs, double *hs, double *gm, double *hm,
-                              cudaStream_t st);
+// PAT_METHOD_LUT (pat_lut.cu): device bytes of the tables of an ns x nm grid, and their
+// construction into buf (lut_bytes(ns, nm) bytes) through scratch (ns nm double2), filling L
+size_t lut_bytes(int ns, int nm);
+cudaError_t launch_lut_tables(int ns, int nm, void *buf, double2 *scratch, LutDev &L, cudaStream_t st);
 
 } // namespace pat
