@@ -387,7 +387,8 @@ def exp1_line(api, dev):
         s = p.forward(x)
         z = torch.empty(w.N, device=dev)
         t = cuda_ms(lambda: (p.forward(x, out=s), p.adjoint(s, out=z)), reps=3)
-        out[name] = {"ms_A_plus_AT": t, "rel_l2_vs_exact": rel_l2(s, s_ex)}
+        out[name] = {"ms_A_plus_AT": t, "rel_l2_vs_exact": rel_l2(s, s_ex),
+                     "quad_evals_per_application": p.info["quad_evals"]}
     out["paper_a100_fp64_ms_per_iteration"] = {"exact": 2021, "lut": 192, "trapezoidal": 145, "point_625": 533,
                                                "piecewise_planes_30": 1256}
     return out
