@@ -11,8 +11,9 @@ any of them (a wrong fold, sign, clamp or branch) shows up as a mismatch.
 
 Further pins: telescoped totals equal the element area, the on-axis piston
 plateau f_i[l] = 2 pi c (Remark on the SIR), the focal-line cylinder formula,
-Remark 1 (group areas are sums of fine areas) and the bin range of
-Eq. (rmin_rmax) against brute-force distances.
+Remark 1 (group areas are sums of fine areas), the bin range of
+Eq. (rmin_rmax) against brute-force distances, and the limit R -> infinity of
+a cylinder (its tangent plane).
 """
 import math
 
@@ -211,3 +212,30 @@ def test_focal_line_cylinder(oracle_mod):
             v1, v2 = -Lz - a3, Lz - a3
             meas = max(0.0, min(v2, vhi) - max(v1, vlo)) + max(0.0, min(v2, -vlo) - max(v1, -vhi))
             assert A == pytest.approx(2 * R * thm * meas, rel=1e-9, abs=1e-20)
+
+
+def test_cylinder_tends_to_the_tangent_plane(oracle_mod):
+    """R -> infinity at fixed arc half-width w and half-height Lz: the
+    cylinder's group areas tend to those of its tangent plane (half sizes w
+    and Lz) at first order in 1/R (the arc's sagitta w^2 / 2R)."""
+    w_arc, Lz, d = 0.5e-3, 0.5e-3, 4.0e-3
+    wl = W.small_cylinder(n_vox=4, L=2048).with_(t0=0.0)
+    e1, e2 = np.array([0.0, 0.0, 1.0]), np.array([1.0, 0.0, 0.0])
+    errs = []
+    for R in (0.05, 0.5, 5.0):
+        c0 = -R * e2  # the surface passes through the origin
+        cyl = W.cylinder_row(c0, e1, e2, R, w_arc / R, Lz)
+        pla = W.plane_row(np.zeros(3), np.cross(e1, e2), e1, w_arc, Lz)
+        xi = np.array([-d, 0.13e-3, -0.21e-3])  # on the concave side, off the element's centre
+        b0, a_c = oracle_mod.pair_bin_areas(cyl, xi, wl)
+        b1, a_p = oracle_mod.pair_bin_areas(pla, xi, wl)
+        lo, hi = min(b0, b1), max(b0 + len(a_c), b1 + len(a_p))
+        ac = np.zeros(hi - lo)
+        ap = np.zeros(hi - lo)
+        ac[b0 - lo:b0 - lo + len(a_c)] = a_c
+        ap[b1 - lo:b1 - lo + len(a_p)] = a_p
+        # compare cumulative areas (robust to a one-bin shift of the range)
+        errs.append(np.abs(np.cumsum(ac) - np.cumsum(ap)).max() / (4 * w_arc * Lz))
+    print("cumulative-area error vs tangent plane", errs)
+    assert errs[0] / errs[1] > 5 and errs[1] / errs[2] > 5, errs
+    assert errs[2] < 1e-3, errs
