@@ -40,6 +40,8 @@
 // the CTA records an error code, finishes what it issued and returns.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "pat_conv_tc.cuh"
 
 namespace pat {
@@ -163,11 +165,12 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b)
 
 // B stage: rows n < kN (transducers k0 + n of src, row length len, row
 // stride ld), columns kk < kKS (source index start + kk); zero outside the
-// row and beyond K.  One 16-byte core-matrix row (8 values) per item.
+// row and beyond K.  One 16-byte core-matrix row (8 values) per item; threads
+// tid = 0 .. nthr - 1 share the items.
 __device__ __forceinline__ void build_b(const float *__restrict__ src, long long ld, int len, int K, int k0, int start,
-                                        uint8_t *bhi, uint8_t *blo)
+                                        uint8_t *bhi, uint8_t *blo, int tid, int nthr)
 {
-    for (int item = threadIdx.x; item < kN * (kKS / 8); item += blockDim.x) {
+    for (int item = tid; item < kN * (kKS / 8); item += nthr) {
         const int n = item / (kKS / 8), q = item % (kKS / 8);
         const int k = k0 + n;
         float v[8];
@@ -182,6 +185,44 @@ __device__ __forceinline__ void build_b(const float *__restrict__ src, long long
             const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * e]), h1 = __float2bfloat16_rn(v[2 * e + 1]);
             const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * e] - __bfloat162float(h0));
             const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * e + 1] - __bfloat162float(h1));
+            h[e] = pack2(h0, h1);
+            l[e] = pack2(l0, l1);
+        }
+        const uint32_t off = op_off(n, q * 8, kN);
+        *reinterpret_cast<uint4 *>(bhi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4 *>(blo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+}
+
+// build_b for exactly kN (kKS / 8) / nthr items per thread, all loads issued
+// before any conversion (memory-level parallelism: the loads of one stage are
+// in flight together instead of one item at a time).
+template <int kItems>
+__device__ __forceinline__ void build_b_batched(const float *__restrict__ src, long long ld, int len, int K, int k0,
+                                                int start, uint8_t *bhi, uint8_t *blo, int tid, int nthr)
+{
+    float v[kItems][8];
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+        const int item = tid + it * nthr;
+        const int n = item / (kKS / 8), q = item % (kKS / 8);
+        const int k = k0 + n;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int m = start + q * 8 + e;
+            v[it][e] = (k < K && m >= 0 && m < len) ? __ldg(&src[(long long)k * ld + m]) : 0.f;
+        }
+    }
+#pragma unroll
+    for (int it = 0; it < kItems; ++it) {
+        const int item = tid + it * nthr;
+        const int n = item / (kKS / 8), q = item % (kKS / 8);
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(v[it][2 * e]), h1 = __float2bfloat16_rn(v[it][2 * e + 1]);
+            const __nv_bfloat16 l0 = __float2bfloat16_rn(v[it][2 * e] - __bfloat162float(h0));
+            const __nv_bfloat16 l1 = __float2bfloat16_rn(v[it][2 * e + 1] - __bfloat162float(h1));
             h[e] = pack2(h0, h1);
             l[e] = pack2(l0, l1);
         }
@@ -312,61 +353,216 @@ struct Pipe {
 } // namespace
 
 // ---------------------------------------------------------------------------
-// Forward: grid (ceil(L / 128), ceil(K / 64)); Tf: nst stages of 2 kAHalf.
+// Forward: grid (ceil(L / 128), ceil(K / 64), nsplit); Tf: nst stages of
+// 2 kAHalf.  CTA z of a tile takes the stages [z nst / nsplit, (z+1) nst /
+// nsplit) and adds its partial tile into s (zeroed by the launcher) when
+// nsplit > 1.
+//
+// Pipeline: a ring of kRing slots, each holding one stage's T (hi, lo) and B
+// (hi, lo).  Warp kIssuerWarp, lane 0, brings T into the slots by bulk copy
+// kLookA stages ahead of the tensor cores and issues each stage's MMAs once
+// its T and B have landed; kRing groups of four warps split B into the slots,
+// group g for the stages of slot g, so that kRing stages load at once.  Slot
+// q % kRing is reused by stage q once the MMAs of stage q - kRing have
+// completed (tcgen05.commit on empty[slot]); T lands on fullA[slot]
+// (transaction count), B on fullB[slot] (one arrival per warp of the group);
+// a last commit on `done` releases the epilogue.  Every barrier is waited on
+// in phase order by each of its waiters, so a parity test never meets a
+// barrier two phases behind.  Every wait gives up after about two seconds or
+// as soon as another thread has given up.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTcThreads) conv_tc_fwd_kernel(const float *__restrict__ f, const uint8_t *__restrict__ Tf,
-                                                                 int nst, int m0off, int K, int L, int UL, int U,
-                                                                 float *__restrict__ s, int *__restrict__ err)
+namespace {
+
+constexpr int kRing = 4, kLookA = 2;
+constexpr int kSlot = 2 * kAHalf + 2 * kBHalf;
+// converter groups of four warps, one per ring slot: group g splits stages
+// g, g + kRing, ..., so that the global loads of several stages are in
+// flight at once, and each slot's empty barrier is waited on by one group, in
+// order (a waiter never runs two phases ahead of a barrier, where the parity
+// test would pass on the older phase)
+constexpr int kConvGroups = kRing, kGroupWarps = 4;
+constexpr int kConvWarps = kConvGroups * kGroupWarps, kIssuerWarp = kConvWarps;
+static_assert(kTcThreadsFwd == 32 * (kConvWarps + 1), "forward block size");
+
+struct Ring {
+    uint8_t *slot[kRing];
+    uint32_t fullA[kRing], fullB[kRing], empty[kRing];
+    uint32_t done; // one phase: every MMA of the CTA has completed
+    uint32_t *tslot;
+    int *abort_flag;
+};
+
+__device__ __forceinline__ Ring carve_ring(uint8_t *base)
+{
+    Ring r;
+    for (int i = 0; i < kRing; ++i) r.slot[i] = base + (size_t)i * kSlot;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + (size_t)kRing * kSlot);
+    for (int i = 0; i < kRing; ++i) {
+        r.fullA[i] = smem_u32(&bars[i]);
+        r.fullB[i] = smem_u32(&bars[kRing + i]);
+        r.empty[i] = smem_u32(&bars[2 * kRing + i]);
+    }
+    r.done = smem_u32(&bars[3 * kRing]);
+    r.tslot = reinterpret_cast<uint32_t *>(&bars[3 * kRing + 1]);
+    r.abort_flag = reinterpret_cast<int *>(&bars[3 * kRing + 2]);
+    return r;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// mbar_wait that also gives up once another thread of the CTA has
+__device__ __forceinline__ bool ring_wait(const Ring &R, uint32_t bar, uint32_t parity)
+{
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity)) {
+        if (*(volatile int *)R.abort_flag) return false;
+        __nanosleep(32);
+        if (clock64() - t0 > kSpinCycles) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void ring_abort(const Ring &R, int *err, int code)
+{
+    *(volatile int *)R.abort_flag = 1;
+    atomicExch(err, code);
+}
+
+} // namespace
+
+__global__ void __launch_bounds__(kTcThreadsFwd, 1)
+    conv_tc_fwd_kernel(const float *__restrict__ f, const uint8_t *__restrict__ Tf, int nst, int m0off, int K, int L,
+                       int UL, int U, float *__restrict__ s, int *__restrict__ err)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    const TcSmem S = carve(smem_raw, 2);
-    const uint32_t tmem = tc_setup(S);
-    const int l0 = blockIdx.x * kM, k0 = blockIdx.y * kN;
-    const long long m0 = (long long)U * l0 + m0off;
-    Pipe pipe;
-    if (threadIdx.x == 0 && !pipe.load(S, Tf, 0)) note_timeout(S, err, 1);
-    for (int st = 0; st < nst; ++st) {
-        const int b = st & 1;
-        uint8_t *bhi = S.b + (size_t)b * 2 * kBHalf;
-        // the B buffer was last read by the MMAs of stage st - 2
-        if (st >= 2 && !*S.abort_flag && !mbar_wait(S.empty[b], ((st - 2) >> 1) & 1)) note_timeout(S, err, 2);
-        __syncthreads();
-        if (*S.abort_flag) break;
-        build_b(f, UL, UL, K, k0, (int)(m0 + (long long)st * kKS), bhi, bhi + kBHalf);
-        fence_proxy_async();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            if (st + 1 < nst && !pipe.load(S, Tf, st + 1)) note_timeout(S, err, 3);
-            else if (!pipe.mma(S, tmem, st, bhi, st == 0)) note_timeout(S, err, 4);
+    const Ring R = carve_ring(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kRing; ++i) {
+            mbar_init(R.fullA[i], 1);
+            mbar_init(R.fullB[i], kGroupWarps);
+            mbar_init(R.empty[i], 1);
         }
+        mbar_init(R.done, 1);
+        *R.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    __syncwarp();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(R.tslot)),
+                     "r"((uint32_t)kN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
     __syncthreads();
-    bool ok = !*S.abort_flag;
-    // the last commit covers every earlier MMA of this thread
-    if (ok && !mbar_wait(S.empty[(nst - 1) & 1], ((nst - 1) >> 1) & 1)) {
-        atomicExch(err, 5);
-        ok = false;
-    }
     fence_after();
-    if (ok) {
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int l = l0 + warp * 32 + lane;
+    const uint32_t tmem = *R.tslot;
+    const int l0 = blockIdx.x * kM, k0 = blockIdx.y * kN;
+    const int st0 = (int)((long long)blockIdx.z * nst / gridDim.z), st1 = (int)((long long)(blockIdx.z + 1) * nst / gridDim.z);
+    const int n = st1 - st0;
+    const long long m0 = (long long)U * l0 + m0off + (long long)st0 * kKS;
+
+    if (warp == kIssuerWarp) {
+        if (lane == 0) {
+            int issued = 0, committed = 0; // T copies started, stages whose MMAs were committed
+            bool ok = true;
+            auto load_a = [&](int q) -> bool {
+                const int b = q % kRing;
+                if (q >= kRing && !ring_wait(R, R.empty[b], ((q / kRing) - 1) & 1)) return false;
+                mbar_expect_tx(R.fullA[b], 2 * kAHalf);
+                bulk_g2s(smem_u32(R.slot[b]), Tf + (size_t)(st0 + q) * 2 * kAHalf, 2 * kAHalf, R.fullA[b]);
+                issued = q + 1;
+                return true;
+            };
+            for (int q = 0; q < kLookA && q < n && ok; ++q) ok = load_a(q);
+            for (int q = 0; q < n && ok; ++q) {
+                if (q + kLookA < n && !load_a(q + kLookA)) {
+                    ok = false;
+                    break;
+                }
+                const int b = q % kRing;
+                if (!ring_wait(R, R.fullA[b], (q / kRing) & 1) || !ring_wait(R, R.fullB[b], (q / kRing) & 1)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                issue_stage(tmem, R.slot[b], R.slot[b] + 2 * kAHalf, R.slot[b] + 2 * kAHalf + kBHalf, q == 0);
+                mma_commit(R.empty[b]);
+                committed = q + 1;
+            }
+            if (ok) mma_commit(R.done); // after the last stage: all of this thread's MMAs
+            if (!ok) {
+                ring_abort(R, err, 4);
+                // bounded waits for the copies and MMAs still in flight
+                for (int q = committed; q < issued; ++q) mbar_wait(R.fullA[q % kRing], (q / kRing) & 1);
+                if (committed > 0) mbar_wait(R.empty[(committed - 1) % kRing], ((committed - 1) / kRing) & 1);
+            }
+        }
+    } else {
+        // converters: B of every stage into its slot.  Lane 0 of each warp
+        // waits and the warp follows its verdict, so that every decision (and
+        // the warp-collective tcgen05.ld below) is warp-uniform.
+        const int grp = warp / kGroupWarps, tid = threadIdx.x - grp * 32 * kGroupWarps;
+        for (int q = grp; q < n; q += kConvGroups) {
+            const int b = q % kRing;
+            int okw = 1;
+            if (q >= kRing) {
+                if (lane == 0) okw = ring_wait(R, R.empty[b], ((q / kRing) - 1) & 1) ? 1 : 0;
+                okw = __shfl_sync(0xffffffffu, okw, 0);
+            }
+            if (!okw) {
+                if (lane == 0) ring_abort(R, err, 2);
+                break;
+            }
+            uint8_t *bh = R.slot[b] + 2 * kAHalf;
+            static_assert(kN * (kKS / 8) % (32 * kGroupWarps) == 0, "items per converter thread");
+            build_b_batched<kN * (kKS / 8) / (32 * kGroupWarps)>(f, UL, UL, K, k0, (int)(m0 + (long long)q * kKS), bh,
+                                                                  bh + kBHalf, tid, 32 * kGroupWarps);
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(R.fullB[b]);
+        }
+        // epilogue (warps 0-3, one per 32 TMEM lanes): wait for all MMAs
+        int ok = 0;
+        if (lane == 0 && warp < 4) {
+            ok = *(volatile int *)R.abort_flag ? 0 : 1;
+            if (ok && !ring_wait(R, R.done, 0)) {
+                ring_abort(R, err, 5);
+                ok = 0;
+            }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        fence_after();
+        if (ok) {
+            const int l = l0 + warp * 32 + lane;
+            const bool split = gridDim.z > 1;
 #pragma unroll 1
-        for (int c = 0; c < kN; c += 16) {
-            float r[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
-            if (l < L) {
+            for (int c = 0; c < kN; c += 16) {
+                float r[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
+                if (l < L) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int k = k0 + c + j;
-                    if (k < K) s[(long long)k * L + l] = r[j];
+                    for (int j = 0; j < 16; ++j) {
+                        const int k = k0 + c + j;
+                        if (k < K) {
+                            if (split) atomicAdd(&s[(long long)k * L + l], r[j]);
+                            else s[(long long)k * L + l] = r[j];
+                        }
+                    }
                 }
             }
         }
-    } else if (threadIdx.x == 0) {
-        pipe.drain(S);
     }
-    tc_teardown(tmem);
+    fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kN)
+                     : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -386,7 +582,7 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_adj_kernel(const float *__
     if (threadIdx.x == 0 && !pipe.load(S, Ta, 0)) note_timeout(S, err, 1);
     for (int st = 0; st < nst; ++st) {
         uint8_t *bhi = S.b + (size_t)st * 2 * kBHalf;
-        build_b(s, L, L, K, k0, m0 + d0 + st * kKS, bhi, bhi + kBHalf);
+        build_b(s, L, L, K, k0, m0 + d0 + st * kKS, bhi, bhi + kBHalf, threadIdx.x, blockDim.x);
     }
     fence_proxy_async();
     __syncthreads();
@@ -514,7 +710,12 @@ TcGeometry tc_geometry(int T, int U, int L, int n_lo)
     g.c = c;
     g.fwd_table_bytes = (size_t)g.nst_fwd * 2 * kAHalf;
     g.adj_table_bytes = (size_t)U * g.nst_adj * 2 * kAHalf;
-    g.fwd_smem = 4 * kAHalf + 2 * 2 * kBHalf + 64;
+    g.fwd_smem = (size_t)kRing * kSlot + 3 * kRing * 8 + 24;
+    int dev = 0;
+    g.sms = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&g.sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+        g.sms = 1;
     g.adj_smem = 4 * kAHalf + (size_t)g.nst_adj * 2 * kBHalf + 64;
     (void)L;
     return g;
@@ -534,8 +735,15 @@ cudaError_t launch_conv_tc_fwd(const float *f, const uint8_t *Tf, const TcGeomet
     cudaError_t e = cudaFuncSetAttribute((const void *)conv_tc_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)g.fwd_smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((L + kM - 1) / kM), (unsigned)((K + kN - 1) / kN));
-    conv_tc_fwd_kernel<<<grid, kTcThreads, g.fwd_smem, st>>>(f, Tf, g.nst_fwd, g.m0off, K, L, U * L, U, s, err);
+    const unsigned gx = (unsigned)((L + kM - 1) / kM), gy = (unsigned)((K + kN - 1) / kN);
+    // split the stages when the tiles alone leave SMs idle (one CTA per SM)
+    int nsplit = std::max(1, std::min(std::min(4, g.nst_fwd), g.sms / (int)(gx * gy)));
+    if (nsplit > 1) {
+        e = cudaMemsetAsync(s, 0, sizeof(float) * (size_t)K * L, st);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid(gx, gy, (unsigned)nsplit);
+    conv_tc_fwd_kernel<<<grid, kTcThreadsFwd, g.fwd_smem, st>>>(f, Tf, g.nst_fwd, g.m0off, K, L, U * L, U, s, err);
     return cudaGetLastError();
 }
 

@@ -11,7 +11,8 @@ namespace pat {
 constexpr int kTcM = 128;      // output samples per tile (MMA M)
 constexpr int kTcN = 64;       // transducers per tile (MMA N)
 constexpr int kTcKStage = 64;  // contraction length per pipeline stage
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 128;     // adjoint kernel
+constexpr int kTcThreadsFwd = 544;  // forward kernel: sixteen converter warps and the issuing warp
 
 // Tile geometry of one plan (taps, U, n_lo fixed).
 struct TcGeometry {
@@ -22,6 +23,7 @@ struct TcGeometry {
     int nst_adj;   // adjoint stages per tile and phase
     size_t fwd_table_bytes, adj_table_bytes;
     size_t fwd_smem, adj_smem; // dynamic shared memory per CTA
+    int sms;                   // SMs of the device (the forward kernel splits its stages to fill them)
 };
 
 TcGeometry tc_geometry(int T, int U, int L, int n_lo);

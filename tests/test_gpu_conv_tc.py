@@ -50,10 +50,13 @@ def _stages(api, orc, w, seed):
     return rel(s, s_ref), rel(v, v_ref)
 
 
-@pytest.mark.parametrize("L,n_angles,n_el", [(1024, 2, 3), (300, 10, 8), (129, 3, 43)])
+@pytest.mark.parametrize("L,n_angles,n_el", [(1024, 2, 3), (300, 10, 8), (129, 3, 43), (1024, 8, 40), (1024, 10, 64)])
 def test_conv_stages_tensor_cores(api, oracle_mod, L, n_angles, n_el):
     """f -> s and s -> v alone: L = 1024 (8 tiles), 300 (ragged), 129 (one
-    sample in the last tile); K = 6, 80 (two transducer tiles), 129."""
+    sample in the last tile); K = 6, 80 (two transducer tiles), 129, and 320
+    and 640, where each CTA of the forward kernel runs its ring of stage
+    buffers several times over (40 tiles with the stages split in three; 80
+    tiles, every stage in one CTA)."""
     w = W.small_cylinder(n_vox=4, n_angles=n_angles, n_el=n_el, L=L)
     es, ev = _stages(api, oracle_mod, w, seed=L)
     assert es <= TC_TOL, es
