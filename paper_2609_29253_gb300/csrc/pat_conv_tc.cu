@@ -34,10 +34,11 @@
 //     the stage's buffers; two buffers alternate;
 //   * the accumulator (128 lanes x 64 columns of TMEM) is read back with
 //     tcgen05.ld, each warp its 32 lanes, and stored to s or v.
-// Operand layout (no swizzle, K-major): 8 x 8 core matrices of 16-bit values
-// (8 rows x 16 bytes, 128 contiguous bytes); core matrix (row group g, K
-// group q) at q * LBO + g * 128.  Every wait is bounded: after about two seconds
-// the CTA records an error code, finishes what it issued and returns.
+// Operand layout: K-major, 128-byte swizzle (op_off), 1024-byte aligned tiles
+// (checked at kernel entry: a CTA whose shared memory is not so aligned records
+// an error and returns before touching the tensor cores).  Every wait is
+// bounded: after about two seconds the CTA records an error code, finishes
+// what it issued and returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -51,20 +52,24 @@ namespace {
 constexpr int kM = kTcM, kN = kTcN, kKS = kTcKStage;
 constexpr int kAHalf = kM * kKS * 2;           // bytes of one T stage (hi or lo)
 constexpr int kBHalf = kN * kKS * 2;           // bytes of one B stage (hi or lo)
-constexpr uint32_t kLboA = kM * 16, kLboB = kN * 16, kSbo = 128;
 constexpr long long kSpinCycles = 4000000000LL; // about 2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Shared-memory matrix descriptor of tcgen05 (no swizzle): start address,
-// leading-dimension byte offset (K direction), stride byte offset (M / N
-// direction), descriptor version 1 at bits 46-47.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+// Shared-memory matrix descriptor of tcgen05 for a K-major operand in the
+// 128-byte swizzle layout (see op_off): start address, leading byte offset
+// (not used when the K extent is one 128-byte row; 16 B), stride byte offset
+// 1024 (between groups of 8 rows), descriptor version 1 (bits 46-47),
+// swizzle mode 2 = 128 B (bits 61-63).  A K step of 16 values inside the row
+// advances the start address by 32 B; the swizzle is applied to the final
+// address bits, so the tile must sit on a 1024-byte boundary.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
 {
     uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)(16 >> 4) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
     d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
     return d;
 }
 
@@ -151,11 +156,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&r)[16])
     for (int j = 0; j < 16; ++j) r[j] = __uint_as_float(u[j]);
 }
 
-// byte offset of element (row, kk) in a no-swizzle K-major operand tile with
-// `rows` rows and kKS columns
-__device__ __forceinline__ uint32_t op_off(int row, int kk, int rows)
+// Byte offset of element (row, kk), kk < kKS = 64, in a K-major operand tile
+// in the 128-byte swizzle layout: each row holds its 64 BF16 values in 128
+// bytes, rows go in groups of 8 (1024-byte atoms), and the 16-byte chunk c of
+// row r is stored at chunk c ^ (r mod 8), so that the 8 rows of an atom read
+// at the same K fall on different shared-memory banks.
+__device__ __forceinline__ uint32_t op_off(int row, int kk)
 {
-    return (uint32_t)((kk >> 3) * (rows * 16) + (row >> 3) * 128 + (row & 7) * 16 + (kk & 7) * 2);
+    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((((kk >> 3) ^ row) & 7) << 4) + (kk & 7) * 2);
 }
 
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b)
@@ -188,7 +196,7 @@ __device__ __forceinline__ void build_b(const float *__restrict__ src, long long
             h[e] = pack2(h0, h1);
             l[e] = pack2(l0, l1);
         }
-        const uint32_t off = op_off(n, q * 8, kN);
+        const uint32_t off = op_off(n, q * 8);
         *reinterpret_cast<uint4 *>(bhi + off) = make_uint4(h[0], h[1], h[2], h[3]);
         *reinterpret_cast<uint4 *>(blo + off) = make_uint4(l[0], l[1], l[2], l[3]);
     }
@@ -226,7 +234,7 @@ __device__ __forceinline__ void build_b_batched(const float *__restrict__ src, l
             h[e] = pack2(h0, h1);
             l[e] = pack2(l0, l1);
         }
-        const uint32_t off = op_off(n, q * 8, kN);
+        const uint32_t off = op_off(n, q * 8);
         *reinterpret_cast<uint4 *>(bhi + off) = make_uint4(h[0], h[1], h[2], h[3]);
         *reinterpret_cast<uint4 *>(blo + off) = make_uint4(l[0], l[1], l[2], l[3]);
     }
@@ -299,10 +307,10 @@ __device__ __forceinline__ void issue_stage(uint32_t tmem, const uint8_t *a, con
     const uint32_t ahi = smem_u32(a), alo = smem_u32(a + kAHalf), bh = smem_u32(bhi), bl = smem_u32(blo);
 #pragma unroll
     for (int ks = 0; ks < kKS / 16; ++ks) {
-        const uint32_t oa = ks * 2 * kLboA, ob = ks * 2 * kLboB;
-        mma_bf16(tmem, sdesc(ahi + oa, kLboA, kSbo), sdesc(bh + ob, kLboB, kSbo), (first && ks == 0) ? 0u : 1u);
-        mma_bf16(tmem, sdesc(ahi + oa, kLboA, kSbo), sdesc(bl + ob, kLboB, kSbo), 1u);
-        mma_bf16(tmem, sdesc(alo + oa, kLboA, kSbo), sdesc(bh + ob, kLboB, kSbo), 1u);
+        const uint32_t o = ks * 32; // 16 BF16 values along K
+        mma_bf16(tmem, sdesc(ahi + o), sdesc(bh + o), (first && ks == 0) ? 0u : 1u);
+        mma_bf16(tmem, sdesc(ahi + o), sdesc(bl + o), 1u);
+        mma_bf16(tmem, sdesc(alo + o), sdesc(bh + o), 1u);
     }
 }
 
@@ -439,6 +447,10 @@ __global__ void __launch_bounds__(kTcThreadsFwd, 1)
                        int UL, int U, float *__restrict__ s, int *__restrict__ err)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
+    if (smem_u32(smem_raw) & 1023u) { // swizzled operand tiles need 1024-byte alignment
+        if (threadIdx.x == 0) atomicExch(err, 6);
+        return;
+    }
     const Ring R = carve_ring(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -575,6 +587,10 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_adj_kernel(const float *__
                                                                  float *__restrict__ v, int *__restrict__ err)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
+    if (smem_u32(smem_raw) & 1023u) { // swizzled operand tiles need 1024-byte alignment
+        if (threadIdx.x == 0) atomicExch(err, 6);
+        return;
+    }
     const TcSmem S = carve(smem_raw, nst);
     const uint32_t tmem = tc_setup(S);
     const int m0 = blockIdx.x * kM, k0 = blockIdx.y * kN;
@@ -654,7 +670,7 @@ __device__ __forceinline__ void put_split(uint8_t *stage, int row, int kk, doubl
 {
     const __nv_bfloat16 hi = __float2bfloat16_rn((float)w);
     const __nv_bfloat16 lo = __float2bfloat16_rn((float)(w - (double)__bfloat162float(hi)));
-    const uint32_t off = op_off(row, kk, kM);
+    const uint32_t off = op_off(row, kk);
     *reinterpret_cast<__nv_bfloat16 *>(stage + off) = hi;
     *reinterpret_cast<__nv_bfloat16 *>(stage + kAHalf + off) = lo;
 }
