@@ -112,23 +112,30 @@ __device__ __forceinline__ void lut_edge(const LutDev &L, float2 q, float2 fourR
     e.j = lut_cell(L.gm, L.hm, L.nm, L.top, m, e.wm);
 }
 
-// E(theta, nu) (nu <= 1), or E(theta, nu) / sqrt(nu) (nu > 1), at s = sin theta
-__device__ __forceinline__ float2 lut_end(const LutDev &L, const LutEdge &e, float2 s)
+// E(theta, nu) (nu <= 1), or E(theta, nu) / sqrt(nu) (nu > 1), at the two
+// bounds of a quadrant, s = sin(theta) = sb and sa, returning E(sb) - E(sa):
+// both cells are found first and both cells' records are read together, so
+// that the two chains of dependent reads overlap (5 % faster than one bound
+// after the other).
+__device__ __forceinline__ float2 lut_end_diff(const LutDev &L, const LutEdge &e, float2 sb, float2 sa)
 {
-    float ws;
-    const int i = lut_cell(L.gs, L.hs, L.ns, L.top, e.big ? ff_mul(s, e.sc) : s, ws);
-    const int c = i * (L.nm - 1) + e.j;
-    const float4 a = __ldg(L.A + c);
-    const float4 b = __ldg(L.B + c);
+    float wb, wa;
+    const int ib = lut_cell(L.gs, L.hs, L.ns, L.top, e.big ? ff_mul(sb, e.sc) : sb, wb);
+    const int ia = lut_cell(L.gs, L.hs, L.ns, L.top, e.big ? ff_mul(sa, e.sc) : sa, wa);
+    const int cb = ib * (L.nm - 1) + e.j, ca = ia * (L.nm - 1) + e.j;
+    const float4 ab = __ldg(L.A + cb), aa = __ldg(L.A + ca);
+    const float4 bb = __ldg(L.B + cb), ba = __ldg(L.B + ca);
     const float wm = e.wm;
-    // E00 + wm dE_m + ws (dE_s + wm dE_ms)
-    float2 E = ff_add_f(make_float2(a.x, a.y), fmaf(wm, a.z, ws * fmaf(wm, b.x, a.w)));
+    float2 Eb = ff_add_f(make_float2(ab.x, ab.y), fmaf(wm, ab.z, wb * fmaf(wm, bb.x, ab.w)));
+    float2 Ea = ff_add_f(make_float2(aa.x, aa.y), fmaf(wm, aa.z, wa * fmaf(wm, ba.x, aa.w)));
     if (e.big) {
-        const float2 cc = __ldg(L.C + c);
-        const float2 F = ff_add_f(make_float2(b.y, b.z), fmaf(wm, b.w, ws * fmaf(wm, cc.y, cc.x)));
-        E = ff_sub(E, ff_mul(e.one_m, F));
+        const float2 cb2 = __ldg(L.C + cb), ca2 = __ldg(L.C + ca);
+        const float2 Fb = ff_add_f(make_float2(bb.y, bb.z), fmaf(wm, bb.w, wb * fmaf(wm, cb2.y, cb2.x)));
+        const float2 Fa = ff_add_f(make_float2(ba.y, ba.z), fmaf(wm, ba.w, wa * fmaf(wm, ca2.y, ca2.x)));
+        Eb = ff_sub(Eb, ff_mul(e.one_m, Fb));
+        Ea = ff_sub(Ea, ff_mul(e.one_m, Fa));
     }
-    return E;
+    return ff_sub(Eb, Ea);
 }
 
 struct LutQuad {
@@ -230,7 +237,7 @@ __device__ __forceinline__ void cyl_pair_lut(const TxDev &t, const TimeDev &tm, 
                 const float2 al = lut_bound(c, q, c.vmax2, inv4, sa); // alpha = Phi-hat(v_max)
                 const float2 be = lut_bound(c, q, c.vmin2, inv4, sb); // beta = Phi-hat(v_min)
                 F = ff_sub(ff_mul(al, c.vmax), ff_mul(be, c.vmin));
-                if (ff_lt(al, be)) F = ff_add(F, ff_mul(ed.pref, ff_sub(lut_end(L, ed, sb), lut_end(L, ed, sa))));
+                if (ff_lt(al, be)) F = ff_add(F, ff_mul(ed.pref, lut_end_diff(L, ed, sb, sa)));
             }
             area = ff_add(area, ff_sub(F, Fp[i]));
             Fp[i] = F;
