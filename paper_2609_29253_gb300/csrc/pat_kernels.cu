@@ -231,13 +231,27 @@ struct FwdDerivSink {
     }
 };
 
+// Consecutive points of a pair that fall in the same bin (neighbouring points
+// of the element) are summed in a register first: one shared-memory FP64
+// atomic per run of equal bins instead of one per point.
 struct FwdPointSink {
     BinWindow w;
     int UL;
     float x;
+    int cb;    // bin of the current run (-1: none)
+    float acc; // its summed weights
+    __device__ __forceinline__ void flush()
+    {
+        if (cb >= w.base && cb <= w.top && cb < UL) atomicAdd((double *)w.hi + (cb - w.base), (double)(x * acc));
+    }
     __device__ __forceinline__ void point(int b, float wt)
     {
-        if (b >= w.base && b <= w.top && b < UL) atomicAdd((double *)w.hi + (b - w.base), (double)(x * wt));
+        if (b != cb) {
+            flush();
+            cb = b;
+            acc = 0.f;
+        }
+        acc += wt;
     }
 };
 
@@ -274,8 +288,9 @@ __global__ void __launch_bounds__(kThreads, 3) fwd_geom_kernel(const TxDev *__re
         if (brick_voxel(g, br, lane, ix, iy, iz)) {
             float xv = x[((long long)iz * g.ny + iy) * g.nx + ix];
             if (METHOD == PAT_METHOD_POINT) {
-                FwdPointSink s{win, tm.UL, xv};
+                FwdPointSink s{win, tm.UL, xv, -1, 0.f};
                 point_pair<KIND>(t, tm, ix, iy, iz, s);
+                s.flush();
             } else {
                 FwdSurfaceSink s{win, xv, 0.f};
                 surface_pair<KIND, false, area_mode(METHOD)>(t, tm, ix, iy, iz, s, glx, glw);
