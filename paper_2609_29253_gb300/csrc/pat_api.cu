@@ -30,10 +30,10 @@ struct pat_plan {
     int T, nW, n_lo;
     int Kf;         // elements after the piecewise-planes expansion (== K without it)
     int *rows;      // per element: its signal row
-    int fwd_chunks; // CTAs per transducer of the forward geometric kernel
+    int fwd_bpc;    // forward geometric kernel: bricks per CTA (super-tile-major order)
+    int fwd_bpc0;   // the chunking the plan-time scan sized fwd_span for (fwd_bpc divides it)
     int adj_wpb;    // warps (voxel bricks) per CTA of the adjoint gather
-    int *fwd_base;  // per transducer: first fine-bin edge of its window
-    int fwd_span;   // window length (edges) common to all transducers
+    int fwd_span;   // forward window length (edges): the largest over its CTAs
     int smem_optin;
     int kind_all;   // PAT_PLANE / PAT_CYLINDER if every element has it, else kKindAny
     double *scal; // device scalars for pat_recon
@@ -232,6 +232,10 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
     g.nby = (g.ny + kBrickY - 1) / kBrickY;
     g.nbz = (g.nz + kBrickZ - 1) / kBrickZ;
     g.nbricks = (long long)g.nbx * g.nby * g.nbz;
+    g.nsx = (g.nbx + kSuper - 1) / kSuper;
+    g.nsy = (g.nby + kSuper - 1) / kSuper;
+    g.nsz = (g.nbz + kSuper - 1) / kSuper;
+    g.nvb = (long long)g.nsx * g.nsy * g.nsz * kSuperBricks;
     TimeDev &tm = p->tm;
     tm.c = params->c;
     tm.t0 = params->t0;
@@ -292,7 +296,6 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
         cudaMalloc(&p->rows, sizeof(int) * (size_t)Kf) != cudaSuccess ||
         cudaMalloc(&p->taps, sizeof(double) * (size_t)n_taps) != cudaSuccess ||
         cudaMalloc(&p->W, sizeof(float) * (size_t)p->nW) != cudaSuccess ||
-        cudaMalloc(&p->fwd_base, sizeof(int) * (size_t)Kf) != cudaSuccess ||
         cudaMalloc(&p->scal, sizeof(double) * 8) != cudaSuccess) {
         cleanup();
         pat_plan_destroy(p);
@@ -339,6 +342,19 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
                 break;
             }
         }
+        // work split of the forward geometric kernel: one super-tile (512
+        // bricks) per CTA, halved until there are 32 CTAs per SM (some ten
+        // waves, so the last one is a small part of the run); the scan below
+        // sizes the window for this chunking, and the autotuner may only
+        // split it further
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        {
+            long long bpc = kSuperBricks;
+            while (bpc > kWarpsPerBlock && (long long)Kf * ((g.nvb + bpc - 1) / bpc) < 32LL * std::max(sms, 1))
+                bpc /= 2;
+            p->fwd_bpc = p->fwd_bpc0 = (int)bpc;
+        }
         // scan every pair once
         void *sbuf = nullptr;
         size_t sb = sizeof(long long) * 6 * (size_t)Kf + 64;
@@ -354,9 +370,10 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
         so.clipped = so.bins + Kf;
         so.quads = so.clipped + Kf;
         so.rmin_bits = so.quads + Kf;
-        std::vector<long long> hb(6 * (size_t)Kf + 1);
-        cudaError_t e = launch_scan(p->tx, Kf, tm, g, so, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), sbuf, sizeof(long long) * (6 * (size_t)Kf + 1),
+        so.maxspan = so.rmin_bits + 1;
+        std::vector<long long> hb(6 * (size_t)Kf + 2);
+        cudaError_t e = launch_scan(p->tx, Kf, tm, g, p->fwd_bpc0, so, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), sbuf, sizeof(long long) * (6 * (size_t)Kf + 2),
                                                   cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         cudaFree(sbuf);
@@ -376,31 +393,14 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
         in.n_lo = n_lo;
         in.bin_lo = 0x7fffffffffffffffLL;
         in.bin_hi = -0x7fffffffffffffffLL;
-        // per-transducer window of the forward difference array: edges of its
-        // pairs lie in [lo, hi + 1]; one bin of margin on either side covers
-        // the point method's FP32 bin decision at the ends of the range
-        std::vector<int> base((size_t)Kf);
-        long long span = 1;
-        for (int k = 0; k < Kf; ++k) {
-            long long lo = hb[k], hi = hb[Kf + k];
-            long long b0 = 0, b1 = 0;
-            if (lo <= hi) {
-                b0 = std::min<long long>(std::max<long long>(lo - 1, 0), tm.UL);
-                b1 = std::max<long long>(std::min<long long>(hi + 2, tm.UL), b0);
-            }
-            base[k] = (int)b0;
-            span = std::max(span, b1 - b0 + 1);
-        }
+        // the forward window: edges of a CTA's pairs lie in [lo, hi + 1] of
+        // its bins, with one bin of margin on either side for the point
+        // method's FP32 bin decision at the ends of the range
+        const long long span = std::max(1LL, hb[6 * (size_t)Kf + 1]);
         p->fwd_span = (int)span;
         if (2 * sizeof(float) * (size_t)span > (size_t)p->smem_optin) {
-            rc = fail(PAT_ERR_UNSUPPORTED, "a transducer's bins span %lld fine bins: %zu bytes of shared memory, "
+            rc = fail(PAT_ERR_UNSUPPORTED, "a forward chunk's bins span %lld fine bins: %zu bytes of shared memory, "
                       "device has %d", span, 2 * sizeof(float) * (size_t)span, p->smem_optin);
-            break;
-        }
-        if (cudaMemcpyAsync(p->fwd_base, base.data(), sizeof(int) * (size_t)Kf, cudaMemcpyHostToDevice, s) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess) {
-            rc = fail(PAT_ERR_CUDA, "pat_plan_create: copy failed");
             break;
         }
         // per element (plane facet); conv_clipped counts elements
@@ -416,14 +416,8 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
         }
         unsigned long long rb = (unsigned long long)hb[6 * (size_t)Kf];
         memcpy(&in.dist_min, &rb, sizeof(double));
-        // work split of the forward geometric kernel: about 8 CTAs per SM in total
-        int sms = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        long long want = (8LL * std::max(sms, 1) + Kf - 1) / Kf;
-        long long maxc = std::max(1LL, g.nbricks / kWarpsPerBlock);
-        p->fwd_chunks = (int)std::max(1LL, std::min(want, maxc));
         p->adj_wpb = kWarpsPerBlock;
-        in.fwd_blocks = (long long)p->fwd_chunks * Kf;
+        in.fwd_blocks = (g.nvb + p->fwd_bpc - 1) / p->fwd_bpc * Kf;
         in.adj_blocks = (g.nbricks + p->adj_wpb - 1) / p->adj_wpb;
         if (!(in.dist_min >= kappa)) {
             rc = fail(PAT_ERR_GEOMETRY, "dist_min = %.6g m < kappa = %.6g m (Assumption 1(iii))", in.dist_min, kappa);
@@ -460,7 +454,6 @@ extern "C" pat_status pat_plan_destroy(pat_plan *p)
     cudaFree(p->tx);
     cudaFree(p->taps);
     cudaFree(p->W);
-    cudaFree(p->fwd_base);
     cudaFree(p->rows);
     cudaFree(p->scal);
     cudaFree(p->tc_fwd_tab);
@@ -532,8 +525,8 @@ static pat_status check_ws(const pat_plan *p, void *ws, size_t bytes, size_t nee
 static pat_status enqueue_forward(pat_plan *p, const float *x, float *s, float *f, void *ws, cudaStream_t st)
 {
     double *D = (double *)ws;
-    CK(launch_fwd_geom(p->tx, p->Kf, p->K, p->rows, p->kind_all, p->tm, p->g, x, D, p->fwd_chunks, p->fwd_base,
-                       p->fwd_span, st));
+    CK(launch_fwd_geom(p->tx, p->Kf, p->K, p->rows, p->kind_all, p->tm, p->g, x, D, p->fwd_bpc, p->fwd_span,
+                       st));
     int mode = p->tm.method == PAT_METHOD_POINT ? 1 : 0;
     if (p->tc && s) {
         float *fw = (float *)((char *)ws + ws_D(p));
@@ -641,8 +634,7 @@ extern "C" pat_status pat_forward_dc(pat_plan *p, const float *x, const double *
     if (st != PAT_OK) return st;
     cudaStream_t cs = (cudaStream_t)stream;
     double *Dg = (double *)ws, *Dd = (double *)((char *)ws + ws_D(p));
-    CK(launch_fwd_geom_dc(p->tx, p->Kf, p->K, p->rows, p->kind_all, p->tm, p->g, x, Dg, Dd, p->fwd_chunks, p->fwd_base,
-                          p->fwd_span,
+    CK(launch_fwd_geom_dc(p->tx, p->Kf, p->K, p->rows, p->kind_all, p->tm, p->g, x, Dg, Dd, p->fwd_bpc, p->fwd_span,
                           cs));
     CK(launch_fwd_dc_epilogue(Dg, Dd, p->W, dtaps, p->T, p->nW, p->n_lo, p->tm, p->K, ds, cs));
     return PAT_OK;
@@ -893,19 +885,16 @@ extern "C" pat_status pat_plan_autotune(pat_plan *p, const float *x, void *ws, s
         }
         return best;
     };
-    // forward: CTAs per transducer
-    const long long maxc = std::max(1LL, p->g.nbricks / kWarpsPerBlock);
-    const int c0 = p->fwd_chunks;
-    int best_c = c0;
+    // forward: bricks per CTA, the planned chunking and its halves and
+    // quarters (each nested in a planned chunk, so within the planned window)
+    const int bpc0 = p->fwd_bpc0;
+    int best_b = bpc0;
     float best_t = 3.0e38f;
-    std::vector<long long> tried;
-    for (int f : {1, 2, 4, 8, 16}) { // c0 / 4 ... 4 c0
-        const long long c = std::max(1LL, std::min(maxc, (long long)c0 * f / 4));
-        if (std::find(tried.begin(), tried.end(), c) != tried.end()) continue;
-        tried.push_back(c);
+    for (int f : {1, 2, 4}) {
+        const int b = bpc0 / f;
+        if (b < kWarpsPerBlock) break;
         const float t = timed([&] {
-            return launch_fwd_geom(p->tx, p->Kf, p->K, p->rows, p->kind_all, p->tm, p->g, x, D, (int)c, p->fwd_base,
-                                   p->fwd_span, cs);
+            return launch_fwd_geom(p->tx, p->Kf, p->K, p->rows, p->kind_all, p->tm, p->g, x, D, b, p->fwd_span, cs);
         });
         if (t < 0.f) {
             cudaEventDestroy(e0);
@@ -914,7 +903,7 @@ extern "C" pat_status pat_plan_autotune(pat_plan *p, const float *x, void *ws, s
         }
         if (t < best_t) {
             best_t = t;
-            best_c = (int)c;
+            best_b = b;
         }
     }
     // adjoint gather: bricks per CTA (the workspace holds finite values from
@@ -937,9 +926,9 @@ extern "C" pat_status pat_plan_autotune(pat_plan *p, const float *x, void *ws, s
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    p->fwd_chunks = best_c;
+    p->fwd_bpc = best_b;
     p->adj_wpb = best_w;
-    p->info.fwd_blocks = (long long)best_c * p->Kf;
+    p->info.fwd_blocks = (p->g.nvb + best_b - 1) / best_b * p->Kf;
     p->info.adj_blocks = (p->g.nbricks + best_w - 1) / best_w;
     return PAT_OK;
 }

@@ -113,22 +113,35 @@ __global__ void scan_init_kernel(ScanOut s, int K)
         s.clipped[k] = 0;
         s.quads[k] = 0;
     }
-    if (k == 0) s.rmin_bits[0] = 0x7ff0000000000000ULL; // +inf
+    if (k == 0) {
+        s.rmin_bits[0] = 0x7ff0000000000000ULL; // +inf
+        s.maxspan[0] = 0;
+    }
 }
 
+// CTA = (aligned run of bricks_per_cta bricks of the super-tile-major order,
+// transducer),
+// the chunking of the forward kernel, so that the largest window any forward
+// CTA needs (s.maxspan) is known before the first launch.
 __global__ void scan_kernel(const TxDev *__restrict__ tx, TimeDev tm, GridDev g, int bricks_per_cta, ScanOut s)
 {
+    __shared__ long long s_lohi[2];
     const int k = blockIdx.y;
     const TxDev &t = tx[k];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        s_lohi[0] = 0x7fffffffffffffffLL;
+        s_lohi[1] = -0x7fffffffffffffffLL;
+    }
+    __syncthreads();
     long long lo = 0x7fffffffffffffffLL, hi = -0x7fffffffffffffffLL;
     unsigned long long groups = 0, bins = 0, clipped = 0, quads = 0;
     double rmin = INFINITY;
-    long long b0 = (long long)blockIdx.x * bricks_per_cta;
-    long long b1 = min(b0 + bricks_per_cta, g.nbricks);
+    const long long b0 = (long long)blockIdx.x * bricks_per_cta, b1 = b0 + bricks_per_cta;
+    const SuperTile stl = super_tile(g, b0);
     for (long long br = b0 + warp; br < b1; br += kWarpsPerBlock) {
         int ix, iy, iz;
-        if (!brick_voxel(g, br, lane, ix, iy, iz)) continue;
+        if (!tile_voxel(g, stl, br, lane, ix, iy, iz)) continue;
         PairRange pr;
         pair_range(t, tm, ix, iy, iz, pr);
         if (pr.bmax < pr.bmin) continue;
@@ -160,6 +173,14 @@ __global__ void scan_kernel(const TxDev *__restrict__ tx, TimeDev tm, GridDev g,
         atomicAdd(&s.clipped[k], clipped);
         atomicAdd(&s.quads[k], quads);
         if (rmin < INFINITY) atomicMin(&s.rmin_bits[0], (unsigned long long)__double_as_longlong(rmin));
+        atomicMin(&s_lohi[0], lo);
+        atomicMax(&s_lohi[1], hi);
+    }
+    __syncthreads();
+    // this CTA's forward window, as fwd_window computes it
+    if (threadIdx.x == 0 && s_lohi[0] <= s_lohi[1]) {
+        const long long base = max(s_lohi[0] - 1, 0LL), top = min(s_lohi[1] + 2, (long long)tm.UL);
+        if (top >= base) atomicMax((unsigned long long *)s.maxspan, (unsigned long long)(top - base + 1));
     }
 }
 
@@ -255,37 +276,84 @@ struct FwdPointSink {
     }
 };
 
-// base[k]: first fine-bin edge of transducer k's window (from the plan-time
-// scan); span: window length shared by all k.  Dg: [K][UL + 1] doubles, zeroed
-// by the launcher; each CTA adds its window into row k.
+// The fine-bin window [base, top] of this CTA (bricks [b0, b1) of super-tile
+// stl): the bins of its pairs (Eq. rmin_rmax), one bin of
+// margin below and two above (the closing edge l_max + 1 of the surface sink
+// and the point method's FP32 bin decision), clipped to [0, U L] and to the
+// `span` bins the launch provides (the plan-time scan sizes it for this
+// chunking, so the clip never bites).  A chunk of bricks close together sees a
+// short range of distances, so the window stays small however far the
+// element's bins spread over the grid.  False when no pair has a bin.
+template <int KIND>
+__device__ bool fwd_window(const TxDev &t, const TimeDev &tm, const GridDev &g, const SuperTile &stl, long long b0,
+                           long long b1, int span, int &base, int &top, int *s_lohi)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        s_lohi[0] = 0x7fffffff;
+        s_lohi[1] = -0x7fffffff;
+    }
+    __syncthreads();
+    int lo = 0x7fffffff, hi = -0x7fffffff;
+    for (long long br = b0 + warp; br < b1; br += kWarpsPerBlock) { // warp-uniform trip count
+        int ix, iy, iz;
+        if (tile_voxel(g, stl, br, lane, ix, iy, iz)) {
+            PairRange pr;
+            pair_range<KIND>(t, tm, ix, iy, iz, pr);
+            if (pr.bmax >= pr.bmin) {
+                lo = min(lo, pr.bmin);
+                hi = max(hi, pr.bmax);
+            }
+        }
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0) {
+        atomicMin(&s_lohi[0], lo);
+        atomicMax(&s_lohi[1], hi);
+    }
+    __syncthreads();
+    lo = s_lohi[0];
+    hi = s_lohi[1];
+    if (lo > hi) return false;
+    base = max(lo - 1, 0);
+    top = min(min(hi + 2, tm.UL), base + span - 1);
+    return top >= base;
+}
+
+// bricks_per_cta: bricks of the super-tile-major order per CTA (blockIdx.x
+// takes the run [blockIdx.x bricks_per_cta, ...), in one super-tile); span:
+// bins of the largest window.  Dg: [K][UL + 1] doubles, zeroed by the launcher; each CTA adds its
+// window into row k.
 // rows[k]: the signal row that element (or plane facet) k adds into; with
 // exclusive != 0 every row has one element, and a CTA that covers its whole
 // element stores its window instead of adding it.
 template <int METHOD, int KIND>
 __global__ void __launch_bounds__(kThreads, 3) fwd_geom_kernel(const TxDev *__restrict__ tx, TimeDev tm, GridDev g,
                                                             const float *__restrict__ x, double *__restrict__ Dg,
-                                                            int bricks_per_cta, const int *__restrict__ base,
-                                                            int span, const int *__restrict__ rows, int exclusive)
+                                                            int bricks_per_cta, int span,
+                                                            const int *__restrict__ rows, int exclusive)
 {
     extern __shared__ float sD[];
     __shared__ float glx[kGLTable], glw[kGLTable];
+    __shared__ int s_lohi[2];
     const int k = blockIdx.y;
     const int n = tm.UL + 1;
-    BinWindow win; // span doubles at sD (the FP64 window, see FwdSurfaceSink)
+    gl_fill(glx, glw, threadIdx.x);
+    const TxDev &t = tx[k];
+    const long long b0 = (long long)blockIdx.x * bricks_per_cta, b1 = b0 + bricks_per_cta;
+    const SuperTile stl = super_tile(g, b0);
+    BinWindow win; // the FP64 window at sD, see FwdSurfaceSink
     win.hi = sD;
     win.lo = nullptr;
-    win.base = base[k];
-    win.top = min(tm.UL, win.base + span - 1);
-    for (int b = threadIdx.x; b < 2 * span; b += blockDim.x) sD[b] = 0.f;
-    gl_fill(glx, glw, threadIdx.x);
+    if (!fwd_window<KIND>(t, tm, g, stl, b0, b1, span, win.base, win.top, s_lohi)) return;
+    const int m = win.top - win.base + 1;
+    for (int b = threadIdx.x; b < 2 * m; b += blockDim.x) sD[b] = 0.f;
     __syncthreads();
-    const TxDev &t = tx[k];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    long long b0 = (long long)blockIdx.x * bricks_per_cta;
-    long long b1 = min(b0 + bricks_per_cta, g.nbricks);
     for (long long br = b0 + warp; br < b1; br += kWarpsPerBlock) { // warp-uniform trip count
         int ix, iy, iz;
-        if (brick_voxel(g, br, lane, ix, iy, iz)) {
+        if (tile_voxel(g, stl, br, lane, ix, iy, iz)) {
             float xv = x[((long long)iz * g.ny + iy) * g.nx + ix];
             if (METHOD == PAT_METHOD_POINT) {
                 FwdPointSink s{win, tm.UL, xv, -1, 0.f};
@@ -300,7 +368,6 @@ __global__ void __launch_bounds__(kThreads, 3) fwd_geom_kernel(const TxDev *__re
     }
     __syncthreads();
     double *row = Dg + (size_t)rows[k] * n + win.base;
-    const int m = win.top - win.base + 1;
     const double *wd = (const double *)sD;
     if (gridDim.x == 1 && exclusive) {
         for (int i = threadIdx.x; i < m; i += blockDim.x) row[i] = wd[i];
@@ -318,38 +385,39 @@ __global__ void __launch_bounds__(kThreads, 3) fwd_geom_kernel(const TxDev *__re
 template <int KIND>
 __global__ void __launch_bounds__(kThreads) fwd_geom_dc_kernel(const TxDev *__restrict__ tx, TimeDev tm, GridDev g,
                                                                const float *__restrict__ x, double *__restrict__ Dg,
-                                                               double *__restrict__ Dd, int bricks_per_cta,
-                                                               const int *__restrict__ base, int span,
+                                                               double *__restrict__ Dd, int bricks_per_cta, int span,
                                                                const int *__restrict__ rows, int exclusive)
 {
     extern __shared__ float sD[];
     __shared__ float glx[kGLTable], glw[kGLTable];
+    __shared__ int s_lohi[2];
     const int k = blockIdx.y;
     const int n = tm.UL + 1;
+    gl_fill(glx, glw, threadIdx.x);
+    const TxDev &t = tx[k];
+    const long long b0 = (long long)blockIdx.x * bricks_per_cta, b1 = b0 + bricks_per_cta;
+    const SuperTile stl = super_tile(g, b0);
     BinWindow win, wind;
     win.hi = sD;
     win.lo = sD + span;
     wind.hi = sD + 2 * span;
     wind.lo = sD + 3 * span;
-    win.base = wind.base = base[k];
-    win.top = wind.top = min(tm.UL, win.base + span - 1);
-    for (int b = threadIdx.x; b < 4 * span; b += blockDim.x) sD[b] = 0.f;
-    gl_fill(glx, glw, threadIdx.x);
+    if (!fwd_window<KIND>(t, tm, g, stl, b0, b1, span, win.base, win.top, s_lohi)) return;
+    wind.base = win.base;
+    wind.top = win.top;
+    const int m = win.top - win.base + 1;
+    for (int b = threadIdx.x; b < m; b += blockDim.x) win.hi[b] = win.lo[b] = wind.hi[b] = wind.lo[b] = 0.f;
     __syncthreads();
-    const TxDev &t = tx[k];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    long long b0 = (long long)blockIdx.x * bricks_per_cta;
-    long long b1 = min(b0 + bricks_per_cta, g.nbricks);
     for (long long br = b0 + warp; br < b1; br += kWarpsPerBlock) {
         int ix, iy, iz;
-        if (brick_voxel(g, br, lane, ix, iy, iz)) {
+        if (tile_voxel(g, stl, br, lane, ix, iy, iz)) {
             FwdDerivSink s{win, wind, x[((long long)iz * g.ny + iy) * g.nx + ix], 0.f, 0.f};
             surface_pair<KIND, true>(t, tm, ix, iy, iz, s, glx, glw);
         }
         __syncwarp();
     }
     __syncthreads();
-    const int m = win.top - win.base + 1;
     double *row = Dg + (size_t)rows[k] * n + win.base, *rowd = Dd + (size_t)rows[k] * n + win.base;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         const double v = (double)win.hi[i] + (double)win.lo[i];
@@ -854,11 +922,18 @@ cudaError_t launch_frames(const double *raw, int K, const double *origin, double
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan(const TxDev *tx, int K, const TimeDev &tm, const GridDev &g, ScanOut s, cudaStream_t st)
+// a forward chunk: a power of two of bricks, at least one per warp, inside one super-tile
+static bool fwd_bpc_ok(int bpc)
 {
+    return bpc >= kWarpsPerBlock && bpc <= kSuperBricks && (bpc & (bpc - 1)) == 0;
+}
+
+cudaError_t launch_scan(const TxDev *tx, int K, const TimeDev &tm, const GridDev &g, int bpc, ScanOut s,
+                        cudaStream_t st)
+{
+    if (!fwd_bpc_ok(bpc)) return cudaErrorInvalidValue;
     scan_init_kernel<<<(K + 255) / 256, 256, 0, st>>>(s, K);
-    int bpc = 64;
-    dim3 grid((unsigned)((g.nbricks + bpc - 1) / bpc), (unsigned)K);
+    dim3 grid((unsigned)(g.nvb / bpc), (unsigned)K);
     scan_kernel<<<grid, kThreads, 0, st>>>(tx, tm, g, bpc, s);
     return cudaGetLastError();
 }
@@ -872,60 +947,55 @@ struct FacetArgs {
 
 template <int METHOD, int KIND>
 static cudaError_t fwd_geom_go(dim3 grid, size_t smem, cudaStream_t st, const TxDev *tx, const TimeDev &tm,
-                               const GridDev &g, const float *x, double *Dg, int bpc, const int *base, int span,
-                               FacetArgs fa)
+                               const GridDev &g, const float *x, double *Dg, int bpc, int span, FacetArgs fa)
 {
     set_smem_attr((const void *)fwd_geom_kernel<METHOD, KIND>, smem);
-    fwd_geom_kernel<METHOD, KIND><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, bpc, base, span, fa.rows,
-                                                                fa.exclusive);
+    fwd_geom_kernel<METHOD, KIND><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, bpc, span, fa.rows, fa.exclusive);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fwd_geom(const TxDev *tx, int Kf, int K, const int *rows, int kind, const TimeDev &tm,
-                            const GridDev &g, const float *x, double *Dg, int chunks, const int *base, int span,
-                            cudaStream_t st)
+                            const GridDev &g, const float *x, double *Dg, int bpc, int span, cudaStream_t st)
 {
+    if (!fwd_bpc_ok(bpc)) return cudaErrorInvalidValue;
     size_t smem = 2 * sizeof(float) * (size_t)span;
-    long long bpc = (g.nbricks + chunks - 1) / chunks;
-    bpc = ((bpc + kWarpsPerBlock - 1) / kWarpsPerBlock) * kWarpsPerBlock;
-    unsigned gx = (unsigned)((g.nbricks + bpc - 1) / bpc);
+    unsigned gx = (unsigned)(g.nvb / bpc);
     cudaError_t e = cudaMemsetAsync(Dg, 0, sizeof(double) * (size_t)(tm.UL + 1) * K, st);
     if (e != cudaSuccess) return e;
     const dim3 grid(gx, (unsigned)Kf);
     const FacetArgs fa{rows, Kf == K ? 1 : 0};
     const int b = (int)bpc;
     if (tm.method == PAT_METHOD_POINT) {
-        if (kind == PAT_PLANE) return fwd_geom_go<PAT_METHOD_POINT, PAT_PLANE>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
+        if (kind == PAT_PLANE) return fwd_geom_go<PAT_METHOD_POINT, PAT_PLANE>(grid, smem, st, tx, tm, g, x, Dg, b, span, fa);
         if (kind == PAT_CYLINDER)
-            return fwd_geom_go<PAT_METHOD_POINT, PAT_CYLINDER>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
-        return fwd_geom_go<PAT_METHOD_POINT, kKindAny>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
+            return fwd_geom_go<PAT_METHOD_POINT, PAT_CYLINDER>(grid, smem, st, tx, tm, g, x, Dg, b, span, fa);
+        return fwd_geom_go<PAT_METHOD_POINT, kKindAny>(grid, smem, st, tx, tm, g, x, Dg, b, span, fa);
     }
     if (tm.method == PAT_METHOD_TRAPEZOID) {
         if (kind == PAT_PLANE)
-            return fwd_geom_go<PAT_METHOD_TRAPEZOID, PAT_PLANE>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
+            return fwd_geom_go<PAT_METHOD_TRAPEZOID, PAT_PLANE>(grid, smem, st, tx, tm, g, x, Dg, b, span, fa);
         if (kind == PAT_CYLINDER)
-            return fwd_geom_go<PAT_METHOD_TRAPEZOID, PAT_CYLINDER>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
-        return fwd_geom_go<PAT_METHOD_TRAPEZOID, kKindAny>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
+            return fwd_geom_go<PAT_METHOD_TRAPEZOID, PAT_CYLINDER>(grid, smem, st, tx, tm, g, x, Dg, b, span, fa);
+        return fwd_geom_go<PAT_METHOD_TRAPEZOID, kKindAny>(grid, smem, st, tx, tm, g, x, Dg, b, span, fa);
     }
     if (tm.method == PAT_METHOD_LUT && kind != PAT_PLANE) { // planes keep their closed form
         if (kind == PAT_CYLINDER)
-            return fwd_geom_go<PAT_METHOD_LUT, PAT_CYLINDER>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
-        return fwd_geom_go<PAT_METHOD_LUT, kKindAny>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
+            return fwd_geom_go<PAT_METHOD_LUT, PAT_CYLINDER>(grid, smem, st, tx, tm, g, x, Dg, b, span, fa);
+        return fwd_geom_go<PAT_METHOD_LUT, kKindAny>(grid, smem, st, tx, tm, g, x, Dg, b, span, fa);
     }
-    if (kind == PAT_PLANE) return fwd_geom_go<PAT_METHOD_SURFACE, PAT_PLANE>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
+    if (kind == PAT_PLANE) return fwd_geom_go<PAT_METHOD_SURFACE, PAT_PLANE>(grid, smem, st, tx, tm, g, x, Dg, b, span, fa);
     if (kind == PAT_CYLINDER)
-        return fwd_geom_go<PAT_METHOD_SURFACE, PAT_CYLINDER>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
-    return fwd_geom_go<PAT_METHOD_SURFACE, kKindAny>(grid, smem, st, tx, tm, g, x, Dg, b, base, span, fa);
+        return fwd_geom_go<PAT_METHOD_SURFACE, PAT_CYLINDER>(grid, smem, st, tx, tm, g, x, Dg, b, span, fa);
+    return fwd_geom_go<PAT_METHOD_SURFACE, kKindAny>(grid, smem, st, tx, tm, g, x, Dg, b, span, fa);
 }
 
 cudaError_t launch_fwd_geom_dc(const TxDev *tx, int Kf, int K, const int *rows, int kind, const TimeDev &tm,
-                               const GridDev &g, const float *x, double *Dg, double *Dd, int chunks, const int *base,
-                               int span, cudaStream_t st)
+                               const GridDev &g, const float *x, double *Dg, double *Dd, int bpc, int span,
+                               cudaStream_t st)
 {
+    if (!fwd_bpc_ok(bpc)) return cudaErrorInvalidValue;
     size_t smem = 4 * sizeof(float) * (size_t)span;
-    long long bpc = (g.nbricks + chunks - 1) / chunks;
-    bpc = ((bpc + kWarpsPerBlock - 1) / kWarpsPerBlock) * kWarpsPerBlock;
-    unsigned gx = (unsigned)((g.nbricks + bpc - 1) / bpc);
+    unsigned gx = (unsigned)(g.nvb / bpc);
     const size_t bytes = sizeof(double) * (size_t)(tm.UL + 1) * K;
     cudaError_t e = cudaMemsetAsync(Dg, 0, bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(Dd, 0, bytes, st);
@@ -937,13 +1007,13 @@ cudaError_t launch_fwd_geom_dc(const TxDev *tx, int Kf, int K, const int *rows, 
                                             : (const void *)fwd_geom_dc_kernel<kKindAny>;
     set_smem_attr(fn, smem);
     if (kind == PAT_PLANE)
-        fwd_geom_dc_kernel<PAT_PLANE><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, Dd, (int)bpc, base, span, rows,
+        fwd_geom_dc_kernel<PAT_PLANE><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, Dd, bpc, span, rows,
                                                                                    excl);
     else if (kind == PAT_CYLINDER)
-        fwd_geom_dc_kernel<PAT_CYLINDER><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, Dd, (int)bpc, base, span, rows,
+        fwd_geom_dc_kernel<PAT_CYLINDER><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, Dd, bpc, span, rows,
                                                                                    excl);
     else
-        fwd_geom_dc_kernel<kKindAny><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, Dd, (int)bpc, base, span, rows,
+        fwd_geom_dc_kernel<kKindAny><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, Dd, bpc, span, rows,
                                                                                    excl);
     return cudaGetLastError();
 }

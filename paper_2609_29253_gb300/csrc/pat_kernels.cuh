@@ -12,18 +12,23 @@ struct ScanOut {
     long long *lo, *hi;                      // extreme fine bins
     unsigned long long *groups, *bins, *clipped, *quads;
     unsigned long long *rmin_bits;           // min distance (bits of a positive double)
+    unsigned long long *maxspan;             // largest forward window (edges) over the CTAs
 };
 
 cudaError_t launch_frames(const double *raw, int K, const double *origin, double pitch, int q1, int q2, TxDev *out,
                           cudaStream_t st);
-cudaError_t launch_scan(const TxDev *tx, int K, const TimeDev &tm, const GridDev &g, ScanOut s, cudaStream_t st);
-// Dg: [K][UL + 1] doubles; base[k], span: fine-bin window of each transducer.
+// bpc: bricks per CTA of the forward kernels the scan sizes the window for
+// (a power of two from kWarpsPerBlock to kSuperBricks, else cudaErrorInvalidValue)
+cudaError_t launch_scan(const TxDev *tx, int K, const TimeDev &tm, const GridDev &g, int bpc, ScanOut s,
+                        cudaStream_t st);
+// Dg: [K][UL + 1] doubles.  CTA (i, k) takes bricks [i bpc, (i + 1) bpc) of the
+// super-tile-major order against element k; span: the largest fine-bin window
+// of a CTA (from the scan with a chunking that bpc divides).
 // kind: PAT_PLANE or PAT_CYLINDER when every descriptor has it, else kKindAny.
 // Kf elements (or plane facets) add into K signal rows, element k into
 // rows[k] (Kf == K: one element per row).
 cudaError_t launch_fwd_geom(const TxDev *tx, int Kf, int K, const int *rows, int kind, const TimeDev &tm,
-                            const GridDev &g, const float *x, double *Dg, int chunks, const int *base, int span,
-                            cudaStream_t st);
+                            const GridDev &g, const float *x, double *Dg, int bpc, int span, cudaStream_t st);
 // in: doubles for mode 0 / 1 (difference array, histogram), floats for mode 2 (f)
 cudaError_t launch_fwd_epilogue(const void *in, int in_stride, const float *W, int nW, int n_lo, const TimeDev &tm,
                                 int mode, int K, float *s, float *f_out, cudaStream_t st);
@@ -37,8 +42,8 @@ cudaError_t launch_taps(int rbf, int eir, double kappa, double c, const double *
                         double *taps, cudaStream_t st, bool dc = false);
 // speed-of-sound derivative: difference arrays of f and of df/dc (fixed bins)
 cudaError_t launch_fwd_geom_dc(const TxDev *tx, int Kf, int K, const int *rows, int kind, const TimeDev &tm,
-                               const GridDev &g, const float *x, double *Dg, double *Dd, int chunks, const int *base,
-                               int span, cudaStream_t st);
+                               const GridDev &g, const float *x, double *Dg, double *Dd, int bpc, int span,
+                               cudaStream_t st);
 cudaError_t launch_fwd_dc_epilogue(const double *Dg, const double *Dd, const float *W, const double *dtaps, int T,
                                    int nW, int n_lo, const TimeDev &tm, int K, float *ds, cudaStream_t st);
 cudaError_t launch_combine_taps(const double *taps, int T, int U, float *W, cudaStream_t st);
