@@ -180,8 +180,9 @@ pat_status pat_system_kernel_dc(const pat_system *sys, double c, double fs, int3
  * q1/q2 < 1 for the point method, frame not orthonormal, theta_max not in
  * (0, pi/2)); PAT_ERR_GEOMETRY (separation, Ass. 1(iii) and Prop. 3);
  * PAT_ERR_WINDOW (bins outside [0, U L) without PAT_FLAG_ALLOW_CLIP);
- * PAT_ERR_UNSUPPORTED (U L too large for the shared-memory histogram, or a
- * tap window too wide for the tensor-core convolution's shared memory);
+ * PAT_ERR_UNSUPPORTED (a forward chunk's bins too many for the shared-memory
+ * window, a pair whose bins the forward kernel's FP32 window bound would miss,
+ * or a tap window too wide for the tensor-core convolution's shared memory);
  * PAT_ERR_CUDA.  *out is NULL on failure. */
 pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, const pat_transducer *tx, int32_t K,
                            const pat_params *params, double kappa, const double *taps_host, int32_t n_taps,

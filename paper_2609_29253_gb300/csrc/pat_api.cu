@@ -371,9 +371,10 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
         so.quads = so.clipped + Kf;
         so.rmin_bits = so.quads + Kf;
         so.maxspan = so.rmin_bits + 1;
-        std::vector<long long> hb(6 * (size_t)Kf + 2);
+        so.misses = so.rmin_bits + 2;
+        std::vector<long long> hb(6 * (size_t)Kf + 3);
         cudaError_t e = launch_scan(p->tx, Kf, tm, g, p->fwd_bpc0, so, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), sbuf, sizeof(long long) * (6 * (size_t)Kf + 2),
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hb.data(), sbuf, sizeof(long long) * (6 * (size_t)Kf + 3),
                                                   cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         cudaFree(sbuf);
@@ -393,11 +394,16 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
         in.n_lo = n_lo;
         in.bin_lo = 0x7fffffffffffffffLL;
         in.bin_hi = -0x7fffffffffffffffLL;
-        // the forward window: edges of a CTA's pairs lie in [lo, hi + 1] of
-        // its bins, with one bin of margin on either side for the point
-        // method's FP32 bin decision at the ends of the range
-        const long long span = std::max(1LL, hb[6 * (size_t)Kf + 1]);
+        // the largest forward window over the CTAs (fwd_window), plus two
+        // bins in case the forward kernel's FP32 bounds round a tie the other
+        // way than the scan's
+        const long long span = hb[6 * (size_t)Kf + 1] + 2;
         p->fwd_span = (int)span;
+        if (hb[6 * (size_t)Kf + 2] != 0) {
+            rc = fail(PAT_ERR_UNSUPPORTED, "pat_plan_create: the FP32 window bound misses the bins of %lld pairs",
+                      hb[6 * (size_t)Kf + 2]);
+            break;
+        }
         if (2 * sizeof(float) * (size_t)span > (size_t)p->smem_optin) {
             rc = fail(PAT_ERR_UNSUPPORTED, "a forward chunk's bins span %lld fine bins: %zu bytes of shared memory, "
                       "device has %d", span, 2 * sizeof(float) * (size_t)span, p->smem_optin);

@@ -116,6 +116,7 @@ __global__ void scan_init_kernel(ScanOut s, int K)
     if (k == 0) {
         s.rmin_bits[0] = 0x7ff0000000000000ULL; // +inf
         s.maxspan[0] = 0;
+        s.misses[0] = 0;
     }
 }
 
@@ -125,26 +126,33 @@ __global__ void scan_init_kernel(ScanOut s, int K)
 // CTA needs (s.maxspan) is known before the first launch.
 __global__ void scan_kernel(const TxDev *__restrict__ tx, TimeDev tm, GridDev g, int bricks_per_cta, ScanOut s)
 {
-    __shared__ long long s_lohi[2];
+    __shared__ int s_lohi[2];
     const int k = blockIdx.y;
     const TxDev &t = tx[k];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        s_lohi[0] = 0x7fffffffffffffffLL;
-        s_lohi[1] = -0x7fffffffffffffffLL;
+        s_lohi[0] = 0x7fffffff;
+        s_lohi[1] = -0x7fffffff;
     }
     __syncthreads();
     long long lo = 0x7fffffffffffffffLL, hi = -0x7fffffffffffffffLL;
-    unsigned long long groups = 0, bins = 0, clipped = 0, quads = 0;
+    int wlo = 0x7fffffff, whi = -0x7fffffff; // pair_bins_fast extremes, as fwd_window
+    unsigned long long groups = 0, bins = 0, clipped = 0, quads = 0, misses = 0;
     double rmin = INFINITY;
     const long long b0 = (long long)blockIdx.x * bricks_per_cta, b1 = b0 + bricks_per_cta;
     const SuperTile stl = super_tile(g, b0);
     for (long long br = b0 + warp; br < b1; br += kWarpsPerBlock) {
         int ix, iy, iz;
         if (!tile_voxel(g, stl, br, lane, ix, iy, iz)) continue;
+        int fb0, fb1;
+        pair_bins_fast(t, tm, ix, iy, iz, fb0, fb1);
+        wlo = min(wlo, fb0);
+        whi = max(whi, fb1);
         PairRange pr;
         pair_range(t, tm, ix, iy, iz, pr);
         if (pr.bmax < pr.bmin) continue;
+        // the window bound pass 1 of the forward kernel takes must hold every edge
+        if (pr.bmin - 1 < fb0 - kWinBelow || pr.bmax + 2 > fb1 + kWinAbove) misses++;
         lo = min(lo, (long long)pr.bmin);
         hi = max(hi, (long long)pr.bmax);
         unsigned long long nb = (unsigned long long)(pr.bmax - pr.bmin + 1);
@@ -163,8 +171,11 @@ __global__ void scan_kernel(const TxDev *__restrict__ tx, TimeDev tm, GridDev g,
         bins += __shfl_xor_sync(0xffffffffu, bins, o);
         clipped += __shfl_xor_sync(0xffffffffu, clipped, o);
         quads += __shfl_xor_sync(0xffffffffu, quads, o);
+        misses += __shfl_xor_sync(0xffffffffu, misses, o);
         rmin = fmin(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
     }
+    wlo = __reduce_min_sync(0xffffffffu, wlo);
+    whi = __reduce_max_sync(0xffffffffu, whi);
     if (lane == 0) {
         atomicMin((long long *)&s.lo[k], lo);
         atomicMax((long long *)&s.hi[k], hi);
@@ -173,13 +184,14 @@ __global__ void scan_kernel(const TxDev *__restrict__ tx, TimeDev tm, GridDev g,
         atomicAdd(&s.clipped[k], clipped);
         atomicAdd(&s.quads[k], quads);
         if (rmin < INFINITY) atomicMin(&s.rmin_bits[0], (unsigned long long)__double_as_longlong(rmin));
-        atomicMin(&s_lohi[0], lo);
-        atomicMax(&s_lohi[1], hi);
+        if (misses) atomicAdd(s.misses, misses);
+        atomicMin(&s_lohi[0], wlo);
+        atomicMax(&s_lohi[1], whi);
     }
     __syncthreads();
     // this CTA's forward window, as fwd_window computes it
-    if (threadIdx.x == 0 && s_lohi[0] <= s_lohi[1]) {
-        const long long base = max(s_lohi[0] - 1, 0LL), top = min(s_lohi[1] + 2, (long long)tm.UL);
+    if (threadIdx.x == 0 && s_lohi[0] <= s_lohi[1] + 2) {
+        const int base = max(s_lohi[0] - kWinBelow, 0), top = min(s_lohi[1] + kWinAbove, tm.UL);
         if (top >= base) atomicMax((unsigned long long *)s.maxspan, (unsigned long long)(top - base + 1));
     }
 }
@@ -277,13 +289,12 @@ struct FwdPointSink {
 };
 
 // The fine-bin window [base, top] of this CTA (bricks [b0, b1) of super-tile
-// stl): the bins of its pairs (Eq. rmin_rmax), one bin of
-// margin below and two above (the closing edge l_max + 1 of the surface sink
-// and the point method's FP32 bin decision), clipped to [0, U L] and to the
-// `span` bins the launch provides (the plan-time scan sizes it for this
-// chunking, so the clip never bites).  A chunk of bricks close together sees a
-// short range of distances, so the window stays small however far the
-// element's bins spread over the grid.  False when no pair has a bin.
+// stl): the bins of its pairs (Eq. rmin_rmax) from pair_bins_fast, widened by
+// kWinBelow and kWinAbove, clipped to [0, U L] and to the `span` bins the
+// launch provides (the plan-time scan sizes it for this chunking, so the clip
+// never bites).  A chunk of bricks close together sees a short range of
+// distances, so the window stays small however far the element's bins spread
+// over the grid.  False when no pair has a bin in [0, U L].
 template <int KIND>
 __device__ bool fwd_window(const TxDev &t, const TimeDev &tm, const GridDev &g, const SuperTile &stl, long long b0,
                            long long b1, int span, int &base, int &top, int *s_lohi)
@@ -298,12 +309,10 @@ __device__ bool fwd_window(const TxDev &t, const TimeDev &tm, const GridDev &g, 
     for (long long br = b0 + warp; br < b1; br += kWarpsPerBlock) { // warp-uniform trip count
         int ix, iy, iz;
         if (tile_voxel(g, stl, br, lane, ix, iy, iz)) {
-            PairRange pr;
-            pair_range<KIND>(t, tm, ix, iy, iz, pr);
-            if (pr.bmax >= pr.bmin) {
-                lo = min(lo, pr.bmin);
-                hi = max(hi, pr.bmax);
-            }
+            int b_lo, b_hi;
+            pair_bins_fast<KIND>(t, tm, ix, iy, iz, b_lo, b_hi);
+            lo = min(lo, b_lo);
+            hi = max(hi, b_hi);
         }
     }
     lo = __reduce_min_sync(0xffffffffu, lo);
@@ -315,9 +324,9 @@ __device__ bool fwd_window(const TxDev &t, const TimeDev &tm, const GridDev &g, 
     __syncthreads();
     lo = s_lohi[0];
     hi = s_lohi[1];
-    if (lo > hi) return false;
-    base = max(lo - 1, 0);
-    top = min(min(hi + 2, tm.UL), base + span - 1);
+    if (lo > hi + 2) return false; // no voxel of the grid in the run
+    base = max(lo - kWinBelow, 0);
+    top = min(min(hi + kWinAbove, tm.UL), base + span - 1);
     return top >= base;
 }
 

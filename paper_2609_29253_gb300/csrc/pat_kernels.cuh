@@ -13,6 +13,7 @@ struct ScanOut {
     unsigned long long *groups, *bins, *clipped, *quads;
     unsigned long long *rmin_bits;           // min distance (bits of a positive double)
     unsigned long long *maxspan;             // largest forward window (edges) over the CTAs
+    unsigned long long *misses;              // pairs whose edges the window bound of pass 1 would miss (0)
 };
 
 cudaError_t launch_frames(const double *raw, int K, const double *origin, double pitch, int q1, int q2, TxDev *out,

@@ -184,6 +184,25 @@ def test_ragged_grid_and_many_tiles(api, orc):
     _run(api, orc, w2)
 
 
+def test_super_tiles_cut_off_in_every_axis(api, orc):
+    """A grid of 2 x 2 x 2 forward super-tiles (32 x 32 x 16 voxels each)
+    that the grid cuts off in every axis, cylinders and planes; the cylinder
+    plan again after the autotuner has timed its forward chunkings.  As in
+    the focal-line test, t0 is off the round values, so that no pair's r_min
+    or r_max ties with a bin edge (the odd grid puts voxels on the focal
+    line); the planes get the time window that holds all their pairs."""
+    n = (37, 45, 21)
+    w = W.small_cylinder(n_vox=8, n_angles=2, n_el=2).with_(n=n, origin=W.centred_origin(n, 0.1e-3), t0=6.00037e-6)
+    w = w.with_(x=W.uniform_phantom(math.prod(n), 6))
+    plan, _, s_ref = _run(api, orc, w, check_stages=False)
+    x = torch.from_numpy(w.x.astype(np.float32)).cuda()
+    shapes = plan.autotune(x)
+    assert shapes["fwd_blocks"] % w.K == 0
+    assert rel(plan.forward(x).cpu().numpy(), s_ref) <= SURF_TOL
+    wp = W.c1().with_(n=n, origin=W.centred_origin(n, 0.1e-3), t0=4.00037e-6, L=512)
+    _run(api, orc, wp.with_(x=W.uniform_phantom(math.prod(n), 7)), check_stages=False)
+
+
 def test_voxels_on_and_near_the_focal_line(api, orc):
     """An odd grid centred on the focal line (voxels at rho = 0 and, after the
     frame rotation by pi, at rho ~ 1e-19 m) seen by the whole 128-element
