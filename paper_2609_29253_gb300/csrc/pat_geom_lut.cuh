@@ -217,6 +217,7 @@ __device__ __forceinline__ void cyl_pair_lut(const TxDev &t, const TimeDev &tm, 
     int e0 = bmin;
     for (int jg = 0; jg < ng; ++jg) {
         const int e1 = min(e0 + dl, bend);
+        sink.pre(e0, e1);
         const float2 tt = ff_from_int_mul(e1 - bmin, tm.fdelta);
         const float2 q = ff_add(qb, ff_mul(tt, ff_add(two_rb, tt)));
         LutEdge ed;

@@ -231,6 +231,7 @@ struct BinWindow {
 struct FwdSurfaceSink {
     BinWindow w;
     float x, prev;
+    __device__ __forceinline__ void pre(int, int) {}
     __device__ __forceinline__ void group(int e0, int, float val, float)
     {
         const float v = x * val;
@@ -248,6 +249,7 @@ struct FwdSurfaceSink {
 struct FwdDerivSink {
     BinWindow w, wd;
     float x, prev, dprev;
+    __device__ __forceinline__ void pre(int, int) {}
     __device__ __forceinline__ void group(int e0, int, float val, float dval)
     {
         const float v = x * val, dv = x * dval;
@@ -650,17 +652,21 @@ struct AdjSurfaceSink {
     int UL;
     float acc;
     float2 pe;  // P at the current group start
+    float2 pn;  // P at its end, loaded by pre()
     bool have;
     __device__ __forceinline__ int clampi(int e) const { return min(max(e, 0), UL); }
-    __device__ __forceinline__ void group(int e0, int e1, float val, float)
+    __device__ __forceinline__ void pre(int e0, int e1)
     {
         if (!have) {
             pe = __ldg(&P[clampi(e0)]);
             have = true;
         }
-        float2 p1 = __ldg(&P[clampi(e1)]);
-        acc = fmaf(val, (p1.x - pe.x) + (p1.y - pe.y), acc);
-        pe = p1;
+        pn = __ldg(&P[clampi(e1)]);
+    }
+    __device__ __forceinline__ void group(int, int, float val, float)
+    {
+        acc = fmaf(val, (pn.x - pe.x) + (pn.y - pe.y), acc);
+        pe = pn;
     }
     __device__ __forceinline__ void finish(int) {}
 };
@@ -699,7 +705,7 @@ __global__ void __launch_bounds__(kThreads, 3) adj_geom_kernel(const TxDev *__re
                 acc += (double)s.acc;
             } else {
                 AdjSurfaceSink s{(const float2 *)Pv + (size_t)rows[k] * stride, tm.UL, 0.f, make_float2(0.f, 0.f),
-                                 false};
+                                 make_float2(0.f, 0.f), false};
                 surface_pair<KIND, false, area_mode(METHOD)>(t, tm, ix, iy, iz, s, glx, glw);
                 acc += (double)s.acc;
             }
