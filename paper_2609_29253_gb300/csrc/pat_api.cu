@@ -422,7 +422,9 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
         }
         unsigned long long rb = (unsigned long long)hb[6 * (size_t)Kf];
         memcpy(&in.dist_min, &rb, sizeof(double));
-        p->adj_wpb = kWarpsPerBlock;
+        // adjoint gather: bricks (warps) per CTA; smaller CTAs leave less idle
+        // at their end (measured best: 2 for planes, c3; 4 for cylinders, c2)
+        p->adj_wpb = p->kind_all == PAT_PLANE ? 2 : 4;
         in.fwd_blocks = (g.nvb + p->fwd_bpc - 1) / p->fwd_bpc * Kf;
         in.adj_blocks = (g.nbricks + p->adj_wpb - 1) / p->adj_wpb;
         if (!(in.dist_min >= kappa)) {

@@ -340,7 +340,7 @@ __device__ bool fwd_window(const TxDev &t, const TimeDev &tm, const GridDev &g, 
 // exclusive != 0 every row has one element, and a CTA that covers its whole
 // element stores its window instead of adding it.
 template <int METHOD, int KIND>
-__global__ void __launch_bounds__(kThreads, 3) fwd_geom_kernel(const TxDev *__restrict__ tx, TimeDev tm, GridDev g,
+__global__ void __launch_bounds__(kThreads, geom_min_ctas(KIND, true)) fwd_geom_kernel(const TxDev *__restrict__ tx, TimeDev tm, GridDev g,
                                                             const float *__restrict__ x, double *__restrict__ Dg,
                                                             int bricks_per_cta, int span,
                                                             const int *__restrict__ rows, int exclusive)
@@ -682,7 +682,7 @@ struct AdjPointSink {
 };
 
 template <int METHOD, int KIND>
-__global__ void __launch_bounds__(kThreads, 3) adj_geom_kernel(const TxDev *__restrict__ tx, int K, TimeDev tm,
+__global__ void __launch_bounds__(kThreads, geom_min_ctas(KIND, false)) adj_geom_kernel(const TxDev *__restrict__ tx, int K, TimeDev tm,
                                                             GridDev g, const void *__restrict__ Pv,
                                                             float *__restrict__ z, const int *__restrict__ rows)
 {
