@@ -15,6 +15,7 @@
 //                        4x4x2 voxels, loop over all transducers, no write
 //                        conflicts (App. G)
 //   taps_kernel          discrete system kernel h-bar (Eq. def_bh), FP64
+#include <algorithm>
 #include <cstdio>
 
 #include "pat_geom.cuh"
@@ -937,6 +938,10 @@ cudaError_t launch_frames(const double *raw, int K, const double *origin, double
     return cudaGetLastError();
 }
 
+// The forward-chunk kernels take the element from blockIdx.y; more elements
+// than a grid's y extent go in slabs of launches.
+constexpr int kMaxGridY = 65535;
+
 // a forward chunk: a power of two of bricks, at least one per warp, inside one super-tile
 static bool fwd_bpc_ok(int bpc)
 {
@@ -948,8 +953,17 @@ cudaError_t launch_scan(const TxDev *tx, int K, const TimeDev &tm, const GridDev
 {
     if (!fwd_bpc_ok(bpc)) return cudaErrorInvalidValue;
     scan_init_kernel<<<(K + 255) / 256, 256, 0, st>>>(s, K);
-    dim3 grid((unsigned)(g.nvb / bpc), (unsigned)K);
-    scan_kernel<<<grid, kThreads, 0, st>>>(tx, tm, g, bpc, s);
+    for (int k0 = 0; k0 < K; k0 += kMaxGridY) { // elements along grid y, in slabs
+        ScanOut sk = s;
+        sk.lo += k0;
+        sk.hi += k0;
+        sk.groups += k0;
+        sk.bins += k0;
+        sk.clipped += k0;
+        sk.quads += k0;
+        const dim3 grid((unsigned)(g.nvb / bpc), (unsigned)std::min(kMaxGridY, K - k0));
+        scan_kernel<<<grid, kThreads, 0, st>>>(tx + k0, tm, g, bpc, sk);
+    }
     return cudaGetLastError();
 }
 
@@ -969,17 +983,10 @@ static cudaError_t fwd_geom_go(dim3 grid, size_t smem, cudaStream_t st, const Tx
     return cudaGetLastError();
 }
 
-cudaError_t launch_fwd_geom(const TxDev *tx, int Kf, int K, const int *rows, int kind, const TimeDev &tm,
-                            const GridDev &g, const float *x, double *Dg, int bpc, int span, cudaStream_t st)
+static cudaError_t fwd_geom_dispatch(dim3 grid, size_t smem, cudaStream_t st, const TxDev *tx, int kind,
+                                     const TimeDev &tm, const GridDev &g, const float *x, double *Dg, int b, int span,
+                                     FacetArgs fa)
 {
-    if (!fwd_bpc_ok(bpc)) return cudaErrorInvalidValue;
-    size_t smem = 2 * sizeof(float) * (size_t)span;
-    unsigned gx = (unsigned)(g.nvb / bpc);
-    cudaError_t e = cudaMemsetAsync(Dg, 0, sizeof(double) * (size_t)(tm.UL + 1) * K, st);
-    if (e != cudaSuccess) return e;
-    const dim3 grid(gx, (unsigned)Kf);
-    const FacetArgs fa{rows, Kf == K ? 1 : 0};
-    const int b = (int)bpc;
     if (tm.method == PAT_METHOD_POINT) {
         if (kind == PAT_PLANE) return fwd_geom_go<PAT_METHOD_POINT, PAT_PLANE>(grid, smem, st, tx, tm, g, x, Dg, b, span, fa);
         if (kind == PAT_CYLINDER)
@@ -1004,6 +1011,21 @@ cudaError_t launch_fwd_geom(const TxDev *tx, int Kf, int K, const int *rows, int
     return fwd_geom_go<PAT_METHOD_SURFACE, kKindAny>(grid, smem, st, tx, tm, g, x, Dg, b, span, fa);
 }
 
+cudaError_t launch_fwd_geom(const TxDev *tx, int Kf, int K, const int *rows, int kind, const TimeDev &tm,
+                            const GridDev &g, const float *x, double *Dg, int bpc, int span, cudaStream_t st)
+{
+    if (!fwd_bpc_ok(bpc)) return cudaErrorInvalidValue;
+    size_t smem = 2 * sizeof(float) * (size_t)span;
+    unsigned gx = (unsigned)(g.nvb / bpc);
+    cudaError_t e = cudaMemsetAsync(Dg, 0, sizeof(double) * (size_t)(tm.UL + 1) * K, st);
+    for (int k0 = 0; k0 < Kf && e == cudaSuccess; k0 += kMaxGridY) {
+        const dim3 grid(gx, (unsigned)std::min(kMaxGridY, Kf - k0));
+        e = fwd_geom_dispatch(grid, smem, st, tx + k0, kind, tm, g, x, Dg, bpc, span,
+                              FacetArgs{rows + k0, Kf == K ? 1 : 0});
+    }
+    return e;
+}
+
 cudaError_t launch_fwd_geom_dc(const TxDev *tx, int Kf, int K, const int *rows, int kind, const TimeDev &tm,
                                const GridDev &g, const float *x, double *Dg, double *Dd, int bpc, int span,
                                cudaStream_t st)
@@ -1015,21 +1037,22 @@ cudaError_t launch_fwd_geom_dc(const TxDev *tx, int Kf, int K, const int *rows, 
     cudaError_t e = cudaMemsetAsync(Dg, 0, bytes, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(Dd, 0, bytes, st);
     if (e != cudaSuccess) return e;
-    const dim3 grid(gx, (unsigned)Kf);
     const int excl = Kf == K ? 1 : 0;
     const void *fn = kind == PAT_PLANE      ? (const void *)fwd_geom_dc_kernel<PAT_PLANE>
                      : kind == PAT_CYLINDER ? (const void *)fwd_geom_dc_kernel<PAT_CYLINDER>
                                             : (const void *)fwd_geom_dc_kernel<kKindAny>;
     set_smem_attr(fn, smem);
-    if (kind == PAT_PLANE)
-        fwd_geom_dc_kernel<PAT_PLANE><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, Dd, bpc, span, rows,
-                                                                                   excl);
-    else if (kind == PAT_CYLINDER)
-        fwd_geom_dc_kernel<PAT_CYLINDER><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, Dd, bpc, span, rows,
-                                                                                   excl);
-    else
-        fwd_geom_dc_kernel<kKindAny><<<grid, kThreads, smem, st>>>(tx, tm, g, x, Dg, Dd, bpc, span, rows,
-                                                                                   excl);
+    for (int k0 = 0; k0 < Kf; k0 += kMaxGridY) {
+        const dim3 grid(gx, (unsigned)std::min(kMaxGridY, Kf - k0));
+        const TxDev *t = tx + k0;
+        const int *r = rows + k0;
+        if (kind == PAT_PLANE)
+            fwd_geom_dc_kernel<PAT_PLANE><<<grid, kThreads, smem, st>>>(t, tm, g, x, Dg, Dd, bpc, span, r, excl);
+        else if (kind == PAT_CYLINDER)
+            fwd_geom_dc_kernel<PAT_CYLINDER><<<grid, kThreads, smem, st>>>(t, tm, g, x, Dg, Dd, bpc, span, r, excl);
+        else
+            fwd_geom_dc_kernel<kKindAny><<<grid, kThreads, smem, st>>>(t, tm, g, x, Dg, Dd, bpc, span, r, excl);
+    }
     return cudaGetLastError();
 }
 

@@ -203,6 +203,26 @@ def test_super_tiles_cut_off_in_every_axis(api, orc):
     _run(api, orc, wp.with_(x=W.uniform_phantom(math.prod(n), 7)), check_stages=False)
 
 
+def test_more_elements_than_a_grid_dimension_holds(api, orc):
+    """66,560 cylindrical positions, more than the 65,535 blocks of a CUDA
+    grid's y or z extent, on a 2 x 2 x 2 grid: the forward chunks and the
+    scan are indexed along one grid dimension.  Three rows of s against the
+    oracle, one from each end and one from the middle."""
+    a = W.C2_ARRAY
+    tx = W.rotated_linear_cylinder_array(a["n_el"], a["el_pitch"], a["R"], a["theta_max"], a["Lz"], 520)
+    n = (2, 2, 2)
+    w = W.c2(angles=np.array([0.0]), with_x=False).with_tx(tx)
+    w = w.with_(n=n, origin=W.centred_origin(n, 0.1e-3), t0=6.00037e-6, x=W.uniform_phantom(8, 3))
+    assert w.K > 65535
+    taps = orc.taps_for(w)
+    plan = api.Plan(w, taps=taps)
+    x32 = w.x.astype(np.float32)
+    s = plan.forward(torch.from_numpy(x32).cuda()).cpu().numpy()
+    ks = [0, 40001, w.K - 1]
+    s_ref = np.stack([orc.forward(w.with_tx(w.tx[k:k + 1]), taps, x32.astype(np.float64))[0][0] for k in ks])
+    assert rel(s[ks], s_ref) <= SURF_TOL, rel(s[ks], s_ref)
+
+
 def test_voxels_on_and_near_the_focal_line(api, orc):
     """An odd grid centred on the focal line (voxels at rho = 0 and, after the
     frame rotation by pi, at rho ~ 1e-19 m) seen by the whole 128-element
