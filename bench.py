@@ -46,7 +46,7 @@ FLOPS_PER_QUAD_EVAL = 166
 # DRAM read + write bytes of one adj_geom_kernel launch of the default
 # workload (128^3 x 512 positions), one-pass ncu capture of this kernel
 # version (29.38 MB read + 16.85 MB written).
-ADJ_TRAFFIC_BYTES = 42.59e6  # adj_geom_kernel DRAM read + write per launch (ncu, full c2 batch)
+ADJ_TRAFFIC_BYTES = 41.94e6  # adj_geom_kernel DRAM read + write per launch (ncu, full c2 batch)
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
