@@ -242,6 +242,40 @@ def conv_compare(api, plan, w, taps, x, dev):
            "rel_l2_tc_vs_fp64": {"forward": rel_l2(s_tc, s_plain), "adjoint": rel_l2(v_tc, v_plain)},
            "step_ms_with_tc": cuda_ms(lambda: (tc.forward(x), tc.adjoint(s_plain)), reps=1)}
     out["tc_error"] = api._lib.pat_plan_get_info(tc.handle)["tc_error"]
+    out["all_c2_rows"] = conv_all_rows(api, taps, dev)
+    return out
+
+
+def conv_all_rows(api, taps, dev):
+    """The same convolutions over all 23,040 c2 positions in one launch (a
+    plan of the c2 time axis and array on an 8^3 grid; the convolution does
+    not depend on the grid), seeded random f, as the tensor cores see a whole
+    c2 application: 360 x 8 output tiles instead of the batch's 8 x 8.
+    FLOP/s counts the tensor-core work as issued (three BF16 products per
+    Toeplitz tile, ~4x the banded multiply-adds)."""
+    import torch
+
+    n = (8, 8, 8)
+    w = W.c2(with_x=False).with_(n=n, origin=W.centred_origin(n, 0.1e-3))
+    plan = api.Plan(w, taps=taps, device=dev)
+    tc = api.Plan(w, taps=taps, conv_tc=True, device=dev)
+    g = torch.Generator(device=dev).manual_seed(7)
+    f = torch.randn((w.K, w.UL), device=dev, generator=g)
+    s_plain = plan.conv_forward(f)
+    s_tc = tc.conv_forward(f)
+    v_plain = plan.conv_adjoint(s_plain)
+    v_tc = tc.conv_adjoint(s_plain)
+    t_tc = cuda_ms(lambda: tc.conv_forward(f), reps=3)
+    nw = w.T + w.U - 1
+    kw = -(-(127 * w.U + nw) // 64) * 64  # Toeplitz contraction length per 128-sample tile
+    flops = 3 * 2 * 128 * 64 * kw * (-(-w.L // 128)) * (-(-w.K // 64))
+    out = {"workload": f"all c2 positions: K {w.K} rows, U L {w.UL} -> L {w.L}, {nw} taps, random f",
+           "forward_ms": {"fp64_cuda_cores": cuda_ms(lambda: plan.conv_forward(f), reps=3), "tcgen05_bf16x3": t_tc},
+           "adjoint_ms": {"fp64_cuda_cores": cuda_ms(lambda: plan.conv_adjoint(s_plain), reps=3),
+                          "tcgen05_bf16x3": cuda_ms(lambda: tc.conv_adjoint(s_plain), reps=3)},
+           "rel_l2_tc_vs_fp64": {"forward": rel_l2(s_tc, s_plain), "adjoint": rel_l2(v_tc, v_plain)},
+           "tcgen05_forward_tflops": flops / (t_tc * 1e-3) / 1e12,
+           "tc_error": api._lib.pat_plan_get_info(tc.handle)["tc_error"]}
     return out
 
 
