@@ -146,7 +146,7 @@ typedef struct pat_plan_info {
     int64_t clipped_pairs;    /* pairs with bins outside [0, U L) */
     int64_t conv_clipped;     /* transducers whose filtered response leaves [0, U L) (dropped by definition) */
     double dist_min;          /* min over pairs of the distance to the element (Eq. min_dist) */
-    int64_t fwd_blocks, adj_blocks;
+    int64_t fwd_blocks, adj_blocks; /* CTAs of one forward / adjoint geometric launch */
     int64_t tc_error;         /* PAT_FLAG_CONV_TC plans: non-zero if a tensor-core CTA gave up waiting on the
                                  TMA engine or the tensor cores (its output tile is then left unwritten);
                                  reading it synchronises with the plan's device */
@@ -261,14 +261,16 @@ pat_status pat_recon_batch(pat_plan *const *plans, int32_t nprob, const float *c
                            const size_t *ws_bytes, void *stream);
 
 /* Autotuner of the launch shapes of one plan: times the forward geometric
- * kernel with c0/4 .. 4 c0 CTAs per transducer (c0 the plan's default) and
- * the adjoint gather with 2, 4 and 8 voxel bricks per CTA, each three times
- * (the first run discarded) on x (device float[N]) and ws
- * (pat_workspace_bytes(plan, PAT_OP_AUTOTUNE) bytes, contents overwritten),
- * and keeps the fastest pair for later calls (pat_plan_info fwd_blocks and
- * adj_blocks report it).  Costs about 13 operator halves; synchronises
- * `stream`, which must not be under capture.  Results of later calls differ
- * from the untuned ones only by the order of floating-point additions. */
+ * kernel with b0, b0/2 and b0/4 voxel bricks per CTA (b0 the plan's default,
+ * a power of two up to one 8 x 8 x 8-brick super-tile; finer runs are never
+ * below one brick per warp) and the adjoint gather with 2, 4 and 8 voxel
+ * bricks per CTA, each three times (the first run discarded) on x (device
+ * float[N]) and ws (pat_workspace_bytes(plan, PAT_OP_AUTOTUNE) bytes,
+ * contents overwritten), and keeps the fastest pair for later calls
+ * (pat_plan_info fwd_blocks and adj_blocks report it).  Costs about 9
+ * operator halves; synchronises `stream`, which must not be under capture.
+ * Results of later calls differ from the untuned ones only by the order of
+ * floating-point additions. */
 pat_status pat_plan_autotune(pat_plan *plan, const float *x, void *ws, size_t ws_bytes, void *stream);
 
 /* s = A x like pat_forward, for callers that cannot allocate device memory
