@@ -54,9 +54,11 @@ enum { PAT_PLANE = 0, PAT_CYLINDER = 1 };
  * (Sec. 4.2.2): E~(s, m) = E(arcsin s, m) and F~(s, m) = F(arcsin s, m) on the
  * power-law grid of Eq. (LUT_sampling) with eps = 1e-16, q1 nodes in s and q2
  * in m, bilinear interpolation, the reciprocal-modulus transformation of
- * Eq. (reciprocal_modulus) for nu > 1.  The tables (16 q1 q2 bytes of device
- * memory, plus the node arrays) are built at plan creation; the arc integral
- * is evaluated in FP64.  Planes keep their closed form. */
+ * Eq. (reciprocal_modulus) for nu > 1.  The tables (one 40-byte record per
+ * grid cell, about 40 q1 q2 bytes of device memory, plus the float-float node
+ * arrays) are built at plan creation from FP64 node values; the arc integral
+ * is evaluated in float-float arithmetic (about 48 significant bits) on the
+ * FP32 units.  Planes keep their closed form. */
 enum { PAT_METHOD_SURFACE = 0, PAT_METHOD_POINT = 1, PAT_METHOD_TRAPEZOID = 2, PAT_METHOD_LUT = 3 };
 enum { PAT_RBF_BUMP = 0, PAT_RBF_CONE = 1, PAT_RBF_WENDLAND = 2 };
 enum { PAT_EIR_GAUSS_SINE = 0, PAT_EIR_BOX = 1 };

@@ -86,6 +86,8 @@ def lib():
                                                C.c_int, C.c_int, C.c_int, _D]
             L.oracle_h_value.restype = C.c_double
             L.oracle_h_value.argtypes = [C.c_int, C.c_double, C.c_int, _D, C.c_double, C.c_int, C.c_double]
+            L.oracle_quad_points.restype = None
+            L.oracle_quad_points.argtypes = [_D, C.c_int, C.c_int, _D, _D]
             L.oracle_num_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -191,6 +193,15 @@ def taps_for(w, panels=3):
 def h_value(rbf_kind, kappa, eir_kind, eir_par, c, t, panels=3):
     return lib().oracle_h_value(int(rbf_kind), float(kappa), int(eir_kind),
                                 np.ascontiguousarray(eir_par, dtype=np.float64), float(c), int(panels), float(t))
+
+
+def quad_points(tx_row, q1, q2):
+    """The point method's Q1 x Q2 points of one element, [Q, 3], and their
+    areas dq [Q] (Alg. 2, Sec. 3.2), point j = j1 q2 + j2."""
+    pts = np.zeros(3 * q1 * q2)
+    dq = np.zeros(q1 * q2)
+    lib().oracle_quad_points(np.ascontiguousarray(tx_row, dtype=np.float64), int(q1), int(q2), pts, dq)
+    return pts.reshape(-1, 3), dq
 
 
 METHOD_SURFACE, METHOD_POINT, METHOD_TRAPEZOID, METHOD_LUT = 0, 1, 2, 3

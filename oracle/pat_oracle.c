@@ -20,7 +20,13 @@
  *     of the area definition built from 3-D geometry (no closed form);
  *   - telescoped totals equal to the aperture area, on-axis piston plateau
  *     f_i[l] = 2 pi c, focal-line cylinder formula;
- *   - system-kernel taps against exact rational integration (box EIR);
+ *   - system-kernel taps against exact rational integration (box EIR), and
+ *     h = e * g and the taps of the Gaussian-modulated sine EIR against
+ *     adaptive Gauss-Kronrod quadrature of Prop. 1 and Eq. (def_bh);
+ *   - the cylinder's point-method quadrature: points on the surface of
+ *     Eq. (cylinder_param), areas summing to R 2 theta_max 2 Lz, midpoint
+ *     sums of closed-form integrands, Q^-1 convergence to the surface
+ *     method (Prop. 2);
  *   - the discrete convolution identity of the sampling operator (App. D);
  *   - the trapezoidal arc integral (Eq. trapezoid_Il): exact on the focal
  *     line (flat level curves), exact group totals, convergence to the exact
@@ -572,6 +578,17 @@ static void quad_point(const double *tx, int q1, int q2, int j1, int j2, double 
         for (int d = 0; d < 3; ++d) pt[d] = c0[d] + R * cos(th) * e2[d] + R * sin(th) * n[d] + z * e1[d];
         *dq = R * (2.0 * thmax / q1) * (2.0 * Lz / q2);
     }
+}
+
+/* Exported for the tests: the Q1 x Q2 points (pts[3 j], j = j1 q2 + j2) and
+ * their areas dq[j] of one element, as Alg. 2 uses them. */
+void oracle_quad_points(const double *tx, int q1, int q2, double *pts, double *dq)
+{
+    for (int j1 = 0; j1 < q1; ++j1)
+        for (int j2 = 0; j2 < q2; ++j2) {
+            const int j = j1 * q2 + j2;
+            quad_point(tx, q1, q2, j1, j2, pts + 3 * (size_t)j, dq + j);
+        }
 }
 
 /* ------------------------------------------------------------------------ */

@@ -958,9 +958,10 @@ extern "C" pat_status pat_forward_static(pat_plan *p, const float *x, float *s, 
     const size_t need = ws_fwd(p);
     if (need > (size_t)PAT_STATIC_SCRATCH_BYTES)
         return fail(PAT_ERR_WORKSPACE,
-                    "pat_forward_static: this plan needs %zu bytes of scratch, the fixed array holds %u "
-                    "(K (U L + 1) 8 bytes must fit; use pat_forward with a caller workspace)",
-                    need, (unsigned)PAT_STATIC_SCRATCH_BYTES);
+                    "pat_forward_static: this plan needs %zu bytes of scratch (%s), the fixed array holds %u; "
+                    "use pat_forward with a caller workspace",
+                    need, p->tc ? "K (U L + 1) 8 + K U L 4 bytes" : "K (U L + 1) 8 bytes",
+                    (unsigned)PAT_STATIC_SCRATCH_BYTES);
     int dev = 0;
     CK(cudaGetDevice(&dev));
     if (dev != p->device) return fail(PAT_ERR_INVALID_ARG, "pat_forward_static: plan belongs to device %d", p->device);

@@ -31,7 +31,8 @@
 //     stored in the operand layout by all threads;
 //   * one thread issues tcgen05.mma (kind::f16, BF16 in, FP32 accumulate,
 //     M = 128, N = 64, K = 16) and tcgen05.commit onto an mbarrier that frees
-//     the stage's buffers; two buffers alternate;
+//     the stage's buffers; the forward kernel cycles a four-slot ring of
+//     stage buffers, the adjoint kernel alternates two;
 //   * the accumulator (128 lanes x 64 columns of TMEM) is read back with
 //     tcgen05.ld, each warp its 32 lanes, and stored to s or v.
 // Operand layout: K-major, 128-byte swizzle (op_off), 1024-byte aligned tiles

@@ -211,3 +211,70 @@ def test_eir_bandwidth():
     # the image at -fc and the +-4 sigma truncation move the edges by ~0.3 %
     assert (band.max() - band.min()) / fc == pytest.approx(0.8, rel=1e-2)
     assert fr[np.argmax(spec)] == pytest.approx(fc, rel=1e-2)
+
+
+# ---------------------------------------------------------------------------
+# Gaussian-modulated sine EIR (the one every benchmark system uses).  The
+# references below are built in this file from Prop. 1, g(t) = -1/2 c t
+# phi(|c t|), with h = e * g, the pulse e(t) = exp(-(t - tc)^2 / (2 s^2))
+# sin(2 pi fc (t - tc)) on [0, Te] (whose bandwidth test_eir_bandwidth pins),
+# and Eq. (def_bh) for the taps, integrated by scipy's adaptive
+# Gauss-Kronrod quadrature, not by the oracle's fixed Gauss-Legendre panels.
+# ---------------------------------------------------------------------------
+def _gauss_sine_ref():
+    integ = pytest.importorskip("scipy.integrate")
+    w = W.c1()
+    fc, s, tc, te = (float(v) for v in w.eir_par)
+    c, kappa = float(w.c), float(w.kappa)
+
+    def phi(r):  # bump radial function (1 - r^2 / kappa^2)^2 on [0, kappa)
+        r = abs(r)
+        return (1.0 - (r / kappa) ** 2) ** 2 if r < kappa else 0.0
+
+    def g(t):
+        return -0.5 * c * t * phi(c * t)
+
+    def e(t):
+        if t < 0.0 or t > te:
+            return 0.0
+        return math.exp(-((t - tc) ** 2) / (2.0 * s * s)) * math.sin(2.0 * math.pi * fc * (t - tc))
+
+    kc = kappa / c
+
+    def h(t):
+        a, b = max(0.0, t - kc), min(te, t + kc)
+        if not b > a:
+            return 0.0
+        pts = [t] if a < t < b else None
+        val, _ = integ.quad(lambda tp: e(tp) * g(t - tp), a, b, points=pts, epsabs=0.0, epsrel=1e-13, limit=200)
+        return val
+
+    return w, integ, h, kc, te
+
+
+def test_h_gauss_sine_eir_vs_adaptive_quadrature(oracle_mod):
+    w, _, h, kc, te = _gauss_sine_ref()
+    ts = np.linspace(-kc, te + kc, 29)[1:-1]
+    ts = np.concatenate([ts, [0.5 * kc, te - 0.3 * kc, w.eir_par[2]]])
+    ref = np.array([h(t) for t in ts])
+    got = np.array([oracle_mod.h_value(w.rbf_kind, w.kappa, W.EIR_GAUSS_SINE, w.eir_par, w.c, t) for t in ts])
+    scale = np.abs(ref).max()
+    assert scale > 0
+    assert np.abs(got - ref).max() <= 1e-11 * scale
+    # outside the support [-kappa/c, Te + kappa/c] the response vanishes
+    for t in (-1.01 * kc, te + 1.01 * kc):
+        assert oracle_mod.h_value(w.rbf_kind, w.kappa, W.EIR_GAUSS_SINE, w.eir_par, w.c, t) == 0.0
+
+
+def test_taps_gauss_sine_eir_vs_adaptive_quadrature(oracle_mod):
+    """h-bar[n] = (1/D) int_{-D}^{D} (D - |s|) h(n D + s) ds (Eq. def_bh)."""
+    w, integ, h, _, _ = _gauss_sine_ref()
+    taps = oracle_mod.taps_for(w)
+    D = 1.0 / (w.U * w.fs)
+    peak = int(np.argmax(np.abs(taps)))
+    picks = sorted({1, 7, peak - 40, peak, peak + 13, w.T // 2, w.T - 3})
+    for t in picks:
+        n = w.n_lo + t
+        val, _ = integ.quad(lambda sv: (D - abs(sv)) * h(n * D + sv), -D, D, points=[0.0], epsabs=0.0, epsrel=1e-12,
+                            limit=100)
+        assert abs(taps[t] - val / D) <= 1e-11 * np.abs(taps).max(), (t, taps[t], val / D)

@@ -191,3 +191,89 @@ def test_linearity(oracle_mod):
     sb, _ = oracle_mod.forward(w, taps, b)
     sab, _ = oracle_mod.forward(w, taps, 2.5 * a - b)
     assert np.abs(sab - (2.5 * sa - sb)).max() <= 1e-12 * np.abs(sab).max()
+
+
+# ---------------------------------------------------------------------------
+# Cylinder branch of the point method (Alg. 2 on the cylinder of
+# Eq. cylinder_param, Sec. 4.2.1): its points must lie on the element and
+# its areas must integrate known functions over the surface exactly (up to
+# the midpoint rule's O(h^2)); the whole point operator must then converge
+# to the surface method's (Prop. 2).
+# ---------------------------------------------------------------------------
+def _tilted_cylinder_row():
+    rng = np.random.default_rng(3)
+    q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    e1, e2 = q[:, 0], q[:, 1]
+    return W.cylinder_row(np.array([1.1e-3, -0.4e-3, 0.7e-3]), e1, e2, 20e-3, math.asin(0.25), 0.15e-3)
+
+
+def test_cylinder_points_lie_on_the_element(oracle_mod):
+    row = _tilted_cylinder_row()
+    c0, e1 = row[1:4], row[4:7]
+    R, thmax, Lz = row[12], row[13], row[14]
+    pts, dq = oracle_mod.quad_points(row, 12, 5)
+    d = pts - c0
+    along = d @ e1
+    radial = d - along[:, None] * e1[None, :]
+    # every point on the cylinder of radius R about the line c0 + t e1, within the strip
+    assert np.abs(np.linalg.norm(radial, axis=1) - R).max() <= 1e-15 * R * 10
+    assert np.abs(along).max() < Lz
+    # the angular aperture: the points' directions from the axis stay within
+    # theta_max of the element's centre direction e2
+    e2 = row[7:10]
+    cosang = radial @ e2 / R
+    assert cosang.min() > math.cos(thmax)
+    # the total area is the element's, R 2 theta_max 2 Lz
+    assert dq.sum() == pytest.approx(R * 2 * thmax * 2 * Lz, rel=1e-14)
+    assert np.all(dq > 0)
+
+
+@pytest.mark.parametrize("q", [(16, 4), (64, 16)])
+def test_cylinder_points_integrate_exactly(oracle_mod, q):
+    """Sum dq f(q_j) against closed-form surface integrals: the midpoint rule
+    is exact for functions affine in the angle and the height, and second
+    order otherwise."""
+    row = _tilted_cylinder_row()
+    c0, e1, e2 = row[1:4], row[4:7], row[7:10]
+    R, thmax, Lz = row[12], row[13], row[14]
+    pts, dq = oracle_mod.quad_points(row, *q)
+    d = pts - c0
+    along = d @ e1
+    radial = d - along[:, None] * e1[None, :]
+    # angle about the axis measured from e2 in the plane normal to e1
+    n = np.cross(e1, e2)
+    ang = np.arctan2(radial @ n, radial @ e2)
+    h1, h2 = 2 * thmax / q[0], 2 * Lz / q[1]
+    # f = angle + height: odd on the symmetric element, integral 0
+    assert abs(np.sum(dq * (ang + along / Lz))) <= 1e-12 * R * thmax * Lz
+    # f = along^2: exact R 2 theta_max (2/3) Lz^3; the midpoint rule is short by R 2 theta_max 2 Lz h2^2 / 12
+    exact = R * 2 * thmax * (2.0 / 3.0) * Lz ** 3
+    mid = exact - R * 2 * thmax * 2 * Lz * h2 ** 2 / 12
+    assert np.sum(dq * along ** 2) == pytest.approx(mid, rel=1e-12)
+    # f = (x - c0) . e2 = R cos(angle): exact 2 R^2 sin(theta_max) 2 Lz; the
+    # midpoint rule for cos on q1 cells gives the closed form below
+    exact_cos = 2 * R * R * math.sin(thmax) * 2 * Lz
+    mid_cos = R * R * 2 * Lz * h1 * sum(math.cos(-thmax + (j + 0.5) * h1) for j in range(q[0]))
+    assert np.sum(dq * (d @ e2)) == pytest.approx(mid_cos, rel=1e-12)
+    assert mid_cos == pytest.approx(exact_cos, rel=h1 ** 2)
+
+
+def test_cylinder_point_method_converges_to_surface_method(oracle_mod):
+    """Prop. 2 on the cylinder: at the same U, the point method's signals
+    approach the surface method's as Q grows, at about the Q^-1 rate."""
+    w = W.small_cylinder(n_vox=6, n_angles=2, n_el=2, dl=1)
+    taps = oracle_mod.taps_for(w)
+    x = w.x.astype(np.float64)
+    ref, _ = oracle_mod.forward(w, taps, x)
+    errs = []
+    for q in (4, 8, 16, 32):
+        wp = w.with_(method=W.METHOD_POINT, q1=q, q2=q)
+        s, _ = oracle_mod.forward(wp, taps, x)
+        errs.append(np.linalg.norm(s - ref) / np.linalg.norm(ref))
+    # Q grows 4x per step: the quadrature term of Prop. 2 falls 4x (measured
+    # 4.2x and 3.9x), until the O(1 / (U F_s)) term, the binning of each
+    # point's 1/r against the surface method's 1/(c tau), is reached at
+    # Q = 32^2 (2.3e-4 at U = 11)
+    assert errs[1] < 0.3 * errs[0], errs
+    assert errs[2] < 0.3 * errs[1], errs
+    assert errs[3] < errs[2] and errs[3] < 5e-4, errs

@@ -41,13 +41,16 @@ def _call_static(_lib, plan, x, s):
     return L.pat_forward_static(plan.handle, C.c_void_p(x.data_ptr()), C.c_void_p(s.data_ptr()), stream)
 
 
-@pytest.mark.parametrize("make", [lambda: W.c1(),
-                                  lambda: W.small_cylinder(n_vox=12, n_angles=4, n_el=3)],
-                         ids=["plane", "cylinder"])
-def test_static_forward_matches_forward(parts, make):
+@pytest.mark.parametrize("make,conv_tc", [(lambda: W.c1(), False),
+                                          (lambda: W.small_cylinder(n_vox=12, n_angles=4, n_el=3), False),
+                                          (lambda: W.small_cylinder(n_vox=12, n_angles=4, n_el=3), True)],
+                         ids=["plane", "cylinder", "cylinder-tensor-core-conv"])
+def test_static_forward_matches_forward(parts, make, conv_tc):
+    """With conv_tc the scratch also holds f (K U L floats after the FP64
+    difference array), which the tensor-core convolution reads."""
     _lib, api, orc = parts
     w = make()
-    plan = api.Plan(w, taps=orc.taps_for(w))
+    plan = api.Plan(w, taps=orc.taps_for(w), conv_tc=conv_tc)
     x = torch.from_numpy(w.x.astype(np.float32)).cuda()
     s_ref = plan.forward(x).cpu().numpy()
     for _ in range(2):  # the scratch keeps the previous call's contents
@@ -60,10 +63,30 @@ def test_static_forward_matches_forward(parts, make):
 def test_static_forward_rejects_oversize_plan(parts):
     _lib, api, orc = parts
     w = W.c1()
-    w = w.with_tx(np.tile(w.tx, (50, 1)))  # 1600 positions: K (U L + 1) 4 bytes > 16 MiB
+    w = w.with_tx(np.tile(w.tx, (50, 1)))  # 1600 positions: K (U L + 1) 8 bytes > 16 MiB
     plan = api.Plan(w, taps=orc.taps_for(w))
     assert _lib.pat_workspace_bytes(plan.handle, _lib.PAT_OP_FORWARD) > (16 << 20)
     x = torch.from_numpy(w.x.astype(np.float32)).cuda()
     s = torch.empty((w.K, w.L), dtype=torch.float32, device="cuda")
     assert _call_static(_lib, plan, x, s) == _lib.PAT_ERR_WORKSPACE
     assert b"fixed array" in _lib.load().pat_last_error()
+
+
+def test_static_forward_rejects_tensor_core_f_beyond_limit(parts):
+    """704 c1 positions: the difference array alone, K (U L + 1) 8 bytes,
+    fits the fixed array; with the tensor-core convolution's f, K U L 4 bytes
+    more, it does not, and only that plan is rejected."""
+    _lib, api, orc = parts
+    w = W.c1()
+    w = w.with_tx(np.tile(w.tx, (22, 1)))
+    taps = orc.taps_for(w)
+    plain = api.Plan(w, taps=taps)
+    tc = api.Plan(w, taps=taps, conv_tc=True)
+    assert _lib.pat_workspace_bytes(plain.handle, _lib.PAT_OP_FORWARD) <= (16 << 20)
+    assert _lib.pat_workspace_bytes(tc.handle, _lib.PAT_OP_FORWARD) > (16 << 20)
+    x = torch.from_numpy(w.x.astype(np.float32)).cuda()
+    s = torch.empty((w.K, w.L), dtype=torch.float32, device="cuda")
+    assert _call_static(_lib, plain, x, s) == 0, _lib.load().pat_last_error()
+    torch.cuda.synchronize()
+    assert _call_static(_lib, tc, x, s) == _lib.PAT_ERR_WORKSPACE
+    assert b"K U L 4 bytes" in _lib.load().pat_last_error()
