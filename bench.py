@@ -65,10 +65,12 @@ def parse():
                    help="voxels per axis over the same 12.8 mm cube (128 = the c2 grid; smaller for profiling)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the convolution, batched-FISTA and c3 comparisons after the main timing")
-    p.add_argument("--extras", default="conv,fista,c3,c5,exp1",
-                   help="comma-separated extra lines to run: conv, fista, c3, c5, exp1")
-    p.add_argument("--fista-problems", type=int, default=8)
-    p.add_argument("--fista-iters", type=int, default=10)
+    p.add_argument("--extras", default="conv,fista,c3,c5,exp1,c1,full",
+                   help="comma-separated extra lines to run: conv, fista, c3, c5, exp1, c1, full")
+    p.add_argument("--fista-first", type=int, default=4, help="first problem of the c4 set")
+    p.add_argument("--fista-problems", type=int, default=4)
+    p.add_argument("--fista-iters", type=int, default=2)
+    p.add_argument("--fista-power", type=int, default=5, help="power iterations for the step size")
     p.add_argument("--c3-positions", type=int, default=128)
     p.add_argument("--c5-positions", type=int, default=16)
     return p.parse_args()
@@ -146,8 +148,9 @@ def physical_gpu_index(local):
     return local
 
 
-def oracle_sample(w, taps, n_vox, seed=0):
-    """Time the FP64 oracle on A and A^T restricted to a seeded voxel subset."""
+def oracle_sample(w, taps, n_vox, seed=0, outputs=False):
+    """Time the FP64 oracle on A and A^T restricted to a seeded voxel subset
+    (taps: the oracle's own system kernel)."""
     import oracle
 
     rng = np.random.default_rng(seed)
@@ -155,10 +158,69 @@ def oracle_sample(w, taps, n_vox, seed=0):
     xs = w.x[idx].astype(np.float64)
     t0 = time.perf_counter()
     s, _ = oracle.forward(w, taps, xs, vox_idx=idx)
-    oracle.adjoint(w, taps, s, vox_idx=idx)
+    z, _ = oracle.adjoint(w, taps, s, vox_idx=idx)
     dt = time.perf_counter() - t0
     pairs = 2 * idx.size * w.K
+    if outputs:
+        return pairs / dt, dt, idx.size, oracle.num_threads(), (idx, s, z)
     return pairs / dt, dt, idx.size, oracle.num_threads()
+
+
+def oracle_parity(api, dev, plan, w, sample, want):
+    """Distances of the CUDA path to the FP64 oracle (rel L2), measured in the
+    CPU-baseline leg, the one part of this script that runs the oracle, on
+    samples the oracle computes in seconds:
+      * the headline batch: A x over the oracle sample's voxels (x zero
+        elsewhere, all rows) and A^T of the oracle's s at those voxels;
+      * c3 (tcgen05 split and plain FP32 plans, first 128 positions): two
+        whole rows of A x and A^T at 256 seeded voxels, per output;
+      * c1: the closed form (dl 1) and the 64 x 64 point method, whole s.
+    Both sides compute their own system kernel."""
+    import torch
+
+    import oracle
+
+    out = {}
+    idx, s_ref, z_ref = sample
+    xs = torch.zeros(w.N, device=dev)
+    xs[torch.from_numpy(idx).to(dev)] = torch.from_numpy(w.x[idx]).to(dev)
+    s_gpu = plan.forward(xs)
+    z_gpu = plan.adjoint(torch.from_numpy(s_ref.astype(np.float32)).to(dev))
+    zg = z_gpu.cpu().numpy()[idx]
+    out["c2_batch"] = {"sample": f"{idx.size} seeded voxels x {w.K} positions",
+                       "A_rel_l2": float(np.linalg.norm(s_gpu.cpu().numpy() - s_ref) / np.linalg.norm(s_ref)),
+                       "AT_rel_l2": float(np.linalg.norm(zg - z_ref) / np.linalg.norm(z_ref))}
+    if "c3" in want:
+        w3 = c3_batch(128)
+        taps3 = oracle.taps_for(w3)
+        ks = np.array([5, 77])
+        x64 = w3.x.astype(np.float64)
+        rows = np.stack([oracle.forward(w3.with_tx(w3.tx[k:k + 1]), taps3, x64)[0][0] for k in ks])
+        rng = np.random.default_rng(5)
+        y = rng.standard_normal((w3.K, w3.L)).astype(np.float32)
+        vidx = np.sort(rng.choice(w3.N, size=256, replace=False)).astype(np.int64)
+        zr, _ = oracle.adjoint(w3, taps3, y.astype(np.float64), vox_idx=vidx)
+        x3 = torch.from_numpy(w3.x).to(dev)
+        res = {"sample": "rows 5 and 77 of A x (all 16.7M voxels); A^T of a seeded y at 256 seeded voxels"}
+        for name, tc in (("tcgen05_split", True), ("plain_fp32", False)):
+            p3 = api.Plan(w3, conv_tc=tc, device=dev)
+            s3 = p3.forward(x3).cpu().numpy()[ks]
+            z3 = p3.adjoint(torch.from_numpy(y).to(dev)).cpu().numpy()[vidx]
+            res[name] = {"A_rows_rel_l2": [float(np.linalg.norm(s3[i] - rows[i]) / np.linalg.norm(rows[i]))
+                                           for i in range(len(ks))],
+                         "AT_rel_l2": float(np.linalg.norm(z3 - zr) / np.linalg.norm(zr))}
+            del p3
+        out["c3"] = res
+    if "c1" in want:
+        res = {}
+        for name, wc in (("closed_form_dl_1", W.c1(dl=1)), ("point_64x64", W.c1(method=W.METHOD_POINT, q=(64, 64),
+                                                                                      dl=1))):
+            ref, _ = oracle.forward(wc, oracle.taps_for(wc), wc.x.astype(np.float64))
+            pc = api.Plan(wc, device=dev)
+            got = pc.forward(torch.from_numpy(wc.x).to(dev)).cpu().numpy()
+            res[name] = {"A_rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+        out["c1"] = res
+    return out
 
 
 def run_reference(args):
@@ -279,16 +341,21 @@ def conv_all_rows(api, taps, dev):
     return out
 
 
-def fista_compare(api, dev, n_prob, iters):
-    """Batched reconstruction (c4-shaped, reduced sizes): n_prob problems of
-    uneven grids, position counts and lengths, s = A x + 1 % noise.  Time per
-    iteration of all problems: one pat_recon per problem enqueued on the
-    legacy stream (plain FP32 operator, no graph), against pat_recon_batch
-    (one CUDA graph per iteration, a branch per problem) with the plain and
-    with the tensor-core-convolution plans."""
+def fista_compare(api, dev, first, n_prob, iters, power):
+    """Batched reconstruction on problems of the c4 set (grids 48^3-160^3,
+    1,024-8,192 planar or cylindrical positions, L 1024 or 2048, tube
+    phantoms), problems first .. first + n_prob - 1, s = A x + 1 % noise,
+    lambda_R = 1e-3 |A^T s|_inf, step from `power` power iterations.  Time per
+    iteration of all problems: one pat_recon per problem enqueued on the legacy
+    stream (plain FP32 operator, no graph), against pat_recon_batch (one CUDA
+    graph per iteration, a branch per problem) with the plain and with the
+    tensor-core-convolution plans.  busy_fraction: the problems' A and A^T
+    device times (CUDA events, one launch sequence each) over the sequential
+    iteration's wall time; 1 - busy is the idle share that persistent
+    kernels or batching could recover."""
     import torch
 
-    ws = [W.c4_problem(p, n_range=(24, 40), k_range=(128, 384)) for p in range(n_prob)]
+    ws = [W.c4_problem(p) for p in range(first, first + n_prob)]
     plans = [api.Plan(w, device=dev) for w in ws]
     plans_tc = [api.Plan(w, taps=p.taps, conv_tc=True, device=dev) for w, p in zip(ws, plans)]
     g = torch.Generator(device=dev).manual_seed(1234)
@@ -300,14 +367,17 @@ def fista_compare(api, dev, n_prob, iters):
         z = p.adjoint(s.contiguous())
         lam.append(float(1e-3 * z.abs().max()))
         v = torch.ones(w.N, device=dev)
-        for _ in range(20):
+        for _ in range(power):
             v = p.adjoint(p.forward((v.double() / v.double().norm()).float()))
         steps.append(float(1.0 / (1.05 * (float(v.double().norm()) + lam[-1]))))
         if not (math.isfinite(lam[-1]) and math.isfinite(steps[-1])):
-            raise RuntimeError(f"{w.name}: lambda {lam[-1]}, step {steps[-1]}, |s0| {float(s0.abs().max())}, "
-                               f"finite s0 {bool(torch.isfinite(s0).all())}, finite z {bool(torch.isfinite(z).all())}, "
-                               f"finite v {bool(torch.isfinite(v).all())}, |x| {float(np.abs(w.x).max())}")
+            raise RuntimeError(f"{w.name}: lambda {lam[-1]}, step {steps[-1]}")
     x0 = [torch.zeros(p.N, device=dev) for p in plans]
+    # device time of one A and one A^T per problem
+    ops_ms = []
+    for p, s in zip(plans, s_list):
+        x = torch.zeros(p.N, device=dev)
+        ops_ms.append(cuda_ms(lambda: (p.forward(x), p.adjoint(s)), reps=1, warm=1))
 
     def seq():
         return [p.recon(s, x, iters=iters, lambda_R=l, step=t) for p, s, x, l, t in zip(plans, s_list, x0, lam, steps)]
@@ -321,7 +391,6 @@ def fista_compare(api, dev, n_prob, iters):
         return r
 
     def wall(fn):
-        fn()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         r = fn()
@@ -334,43 +403,64 @@ def fista_compare(api, dev, n_prob, iters):
     d_b = max(rel_l2(a, b) for a, b in zip(r_b, r_seq))
     d_tc = max(rel_l2(a, b) for a, b in zip(r_tc, r_seq))
     pairs = sum(w.N * w.K for w in ws)
-    return {"workload": "; ".join(w.name for w in ws), "problems": n_prob, "iterations": iters,
-            "pairs_per_iteration": 2 * pairs,
+    return {"workload": "; ".join(w.name for w in ws),
+            "selection": f"c4 problems {first}..{first + n_prob - 1} (seeds 1000 + p) of the 32 drawn from the "
+                         f"stated ranges; {iters} iterations each, step from {power} power iterations",
+            "problems": n_prob, "iterations": iters, "pairs_per_iteration": 2 * pairs,
             "ms_per_iteration": {"plain_fp32_sequential": t_seq, "graph_batched": t_b,
                                  "graph_batched_tcgen05_conv": t_tc},
             "speedup_vs_plain": {"graph_batched": t_seq / t_b, "graph_batched_tcgen05_conv": t_seq / t_tc},
             "max_rel_l2_vs_plain": {"graph_batched": d_b, "graph_batched_tcgen05_conv": d_tc},
+            "ms_A_plus_AT_per_problem": ops_ms, "busy_fraction_sequential": sum(ops_ms) / t_seq,
+            "pairs_per_s_sequential": 2 * pairs / (t_seq * 1e-3),
             "timing": "wall clock per iteration over all problems, host to device completion, step sizes fixed"}
 
 
 def c3_line(api, dev, n_pos):
     """The precision-split system (c3): 256^3 voxels at 0.08 mm, planar 3x3 mm
     elements on a 40 mm hemisphere, L 2048, tcgen05 BF16 split convolution;
-    one batch of the first n_pos positions."""
+    one batch of the first n_pos positions, against the plain FP32 plan
+    (FP64-accumulated convolution on the CUDA cores) on the same positions."""
     import torch
 
-    w = W.c3(with_x=False, rotations=1)
-    w = w.with_tx(w.tx[:n_pos])
-    w = w.with_(x=W.blob_phantom(w.n, w.origin, w.pitch, 200, 0))
+    w = c3_batch(n_pos)
     plan = api.Plan(w, conv_tc=True, device=dev)
+    plain = api.Plan(w, taps=plan.taps, device=dev)
     x = torch.from_numpy(w.x).to(dev)
     s = plan.forward(x)
     t_f = cuda_ms(lambda: plan.forward(x, out=s), reps=2)
     z = torch.empty(w.N, device=dev)
     t_a = cuda_ms(lambda: plan.adjoint(s, out=z), reps=2)
+    s_p = plain.forward(x)
+    t_pf = cuda_ms(lambda: plain.forward(x, out=s_p), reps=2)
+    z_p = torch.empty(w.N, device=dev)
+    t_pa = cuda_ms(lambda: plain.adjoint(s, out=z_p), reps=2)
     pairs = w.N * w.K
     return {"workload": f"c3: 256^3 @ 0.08 mm, first {w.K} of 5,120 planar 3x3 mm positions, L 2048 @ 40 MHz, "
                         f"U 11, dl 11, tcgen05 BF16 split convolution",
             "forward_pairs_per_s": pairs / (t_f * 1e-3), "adjoint_pairs_per_s": pairs / (t_a * 1e-3),
             "ms": {"forward": t_f, "adjoint": t_a}, "mean_bins_per_pair": plan.info["pair_bins"] / pairs,
+            "plain_fp32": {"ms": {"forward": t_pf, "adjoint": t_pa},
+                           "forward_pairs_per_s": pairs / (t_pf * 1e-3), "adjoint_pairs_per_s": pairs / (t_pa * 1e-3)},
+            "rel_l2_split_vs_plain_fp32": {"forward": rel_l2(s, s_p), "adjoint": rel_l2(z, z_p)},
             "tc_error": api._lib.pat_plan_get_info(plan.handle)["tc_error"]}
+
+
+def c3_batch(n_pos):
+    w = W.c3(with_x=False, rotations=1)
+    w = w.with_tx(w.tx[:n_pos])
+    return w.with_(x=W.blob_phantom(w.n, w.origin, w.pitch, 200, 0))
 
 
 def c5_line(api, dev, n_pos):
     """The full-scale system (c5): 512^3 voxels at 0.05 mm (134M), the c2
     array rotated over 128 angles, L 4096 at 50 MHz; the first n_pos
     positions of one angle, closed form (surface method) against the point
-    method with 16 x 16 points per element (Alg. 2) on a quarter of them."""
+    method with 16 x 16 points per element (Alg. 2) on a quarter of them.
+    The point method bins each point per fine bin, so its distance to the
+    closed form is reported both against the closed form at the same
+    binning (dl = 1: the quadrature error, Prop. 2) and at the operating
+    point dl = U (which adds Remark 1's grouping)."""
     import torch
 
     w = W.c5(with_x=False, n_angles=128)
@@ -387,6 +477,8 @@ def c5_line(api, dev, n_pos):
     pplan = api.Plan(wp, taps=plan.taps, device=dev)
     sp = pplan.forward(x)
     t_pf = cuda_ms(lambda: pplan.forward(x, out=sp), reps=1)
+    plan1 = api.Plan(w.with_tx(w.tx[:n_pt]).with_(dl=1), taps=plan.taps, device=dev)
+    s1 = plan1.forward(x)
     pairs = w.N * w.K
     return {"workload": f"c5: 512^3 @ 0.05 mm, first {w.K} of 16,384 cylindrical positions, L 4096 @ 50 MHz, U 11, "
                         f"dl 11; point method 16 x 16 on the first {n_pt}",
@@ -394,7 +486,70 @@ def c5_line(api, dev, n_pos):
                             "ms": {"forward": t_f, "adjoint": t_a}},
             "point_16x16": {"forward_pairs_per_s": w.N * n_pt / (t_pf * 1e-3), "ms": {"forward": t_pf},
                             "point_evaluations_per_s": w.N * n_pt * 256 / (t_pf * 1e-3)},
+            "point_16x16_vs_closed_form_rel_l2": {"same_binning_dl_1": rel_l2(sp, s1),
+                                                  "operating_point_dl_11": rel_l2(sp, s[:n_pt])},
             "mean_bins_per_pair": plan.info["pair_bins"] / pairs}
+
+
+def c1_line(api, dev):
+    """The c1 system (16^3 voxels at 0.1 mm, 32 planar 1 x 1 mm elements on a
+    10 mm Fibonacci sphere, L 256 at 40 MHz): the closed form against the
+    64 x 64 point quadrature of the surface (Alg. 2), at the same binning
+    (dl = 1) and with the closed form at its operating point dl = U."""
+    import torch
+
+    w1 = W.c1(dl=1)
+    x = torch.from_numpy(w1.x).to(dev)
+    taps = api.system_taps(w1, dev)
+    closed1 = api.Plan(w1, taps=taps, device=dev)
+    closed11 = api.Plan(W.c1(), taps=taps, device=dev)
+    point = api.Plan(W.c1(method=W.METHOD_POINT, q=(64, 64), dl=1), taps=taps, device=dev)
+    out = {"workload": w1.name + "; closed form (dl 1 and 11) and 64 x 64 points per element"}
+    res = {}
+    for name, p in (("closed_form_dl_1", closed1), ("closed_form_dl_11", closed11), ("point_64x64", point)):
+        s = p.forward(x)
+        z = torch.empty(w1.N, device=dev)
+        res[name] = s
+        out[name] = {"ms_A_plus_AT": cuda_ms(lambda: (p.forward(x, out=s), p.adjoint(s, out=z)), reps=3)}
+    out["point_64x64_vs_closed_form_rel_l2"] = {"same_binning_dl_1": rel_l2(res["point_64x64"], res["closed_form_dl_1"]),
+                                                "operating_point_dl_11": rel_l2(res["point_64x64"],
+                                                                                res["closed_form_dl_11"])}
+    return out
+
+
+def full_line(api, dev, x2):
+    """Whole applications of the headline systems: one A and one A^T over all
+    23,040 c2 positions (128^3 voxels), and over all 5,120 c3 positions
+    (256^3 voxels, tcgen05 BF16 split convolution), CUDA events, clocks
+    sampled during the run."""
+    import torch
+
+    out = {}
+    w2 = W.c2(with_x=False)
+    w3 = W.c3(with_x=False)
+    w3 = w3.with_(x=W.blob_phantom(w3.n, w3.origin, w3.pitch, 200, 0))
+    for name, w, x, tc in (("c2_all_23040_positions", w2, x2, False),
+                           ("c3_all_5120_positions", w3, None, True)):
+        t0 = time.perf_counter()
+        plan = api.Plan(w, conv_tc=tc, device=dev)
+        t_plan = time.perf_counter() - t0
+        if x is None:
+            x = torch.from_numpy(w.x).to(dev)
+        s = torch.empty((w.K, w.L), device=dev)
+        z = torch.empty(w.N, device=dev)
+        clk = ClockSampler(physical_gpu_index(torch.cuda.current_device()))
+        clk.start()
+        t_f = cuda_ms(lambda: plan.forward(x, out=s), reps=1, warm=0)
+        t_a = cuda_ms(lambda: plan.adjoint(s, out=z), reps=1, warm=0)
+        c = clk.stop()
+        pairs = w.N * w.K
+        out[name] = {"ms": {"A": t_f, "AT": t_a, "A_plus_AT": t_f + t_a}, "pairs": pairs,
+                     "pairs_per_s": 2 * pairs / ((t_f + t_a) * 1e-3), "forward_pairs_per_s": pairs / (t_f * 1e-3),
+                     "adjoint_pairs_per_s": pairs / (t_a * 1e-3), "plan_creation_s": t_plan, "clocks": c,
+                     "tc_error": api._lib.pat_plan_get_info(plan.handle)["tc_error"] if tc else None}
+        del plan, s, z
+        torch.cuda.empty_cache()
+    return out
 
 
 def exp1_line(api, dev):
@@ -554,9 +709,11 @@ def main():
 
         oracle.build()
         wcpu = c2w(args, angle_sets[args.warmup], with_x=False).with_(x=w0.x)
-        v, dt, nv, cores = oracle_sample(wcpu, taps, args.cpu_sample_voxels)
+        v, dt, nv, cores, smp = oracle_sample(wcpu, oracle.taps_for(wcpu), args.cpu_sample_voxels, outputs=True)
         cpu = {"value": v, "unit": "pairs/s", "cores": cores, "kind": "oracle",
                "sample": f"{nv} seeded voxels x {wcpu.K} positions, A then A^T, FP64 ({dt:.1f} s)"}
+        want_p = set(e.strip() for e in args.extras.split(",")) if not args.no_extras else set()
+        cpu["parity"] = oracle_parity(api, dev, plans[args.warmup], wcpu, smp, want_p)
 
     extras = {}
     want = set(e.strip() for e in args.extras.split(",") if e.strip())
@@ -566,13 +723,22 @@ def main():
                                                   c2w(args, angle_sets[args.warmup], with_x=False).with_(x=w0.x), taps,
                                                   x, dev)
         if "fista" in want:
-            extras["fista_batched"] = fista_compare(api, dev, args.fista_problems, args.fista_iters)
+            extras["fista_batched"] = fista_compare(api, dev, args.fista_first, args.fista_problems, args.fista_iters,
+                                                    args.fista_power)
         if "c3" in want:
             extras["c3_precision_split"] = c3_line(api, dev, args.c3_positions)
+            if cpu and "c3" in cpu.get("parity", {}):
+                extras["c3_precision_split"]["rel_l2_vs_fp64_oracle"] = cpu["parity"]["c3"]
         if "c5" in want and args.c5_positions > 0:
             extras["c5_full_scale_subset"] = c5_line(api, dev, args.c5_positions)
         if "exp1" in want:
             extras["exp1_operators"] = exp1_line(api, dev)
+        if "c1" in want:
+            extras["c1_closed_vs_quadrature"] = c1_line(api, dev)
+            if cpu and "c1" in cpu.get("parity", {}):
+                extras["c1_closed_vs_quadrature"]["rel_l2_vs_fp64_oracle"] = cpu["parity"]["c1"]
+        if "full" in want and args.grid == 128:
+            extras["full_applications"] = full_line(api, dev, x)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,

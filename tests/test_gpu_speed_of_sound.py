@@ -150,3 +150,22 @@ def test_autograd_speed_of_sound_gradient(api, oracle_mod):
     # the x-gradient is A^T (A x - y)
     gx = plan.adjoint((s.detach() - torch.from_numpy(y).cuda()).contiguous())
     assert torch.allclose(x.grad, gx, rtol=1e-4, atol=1e-6 * float(gx.abs().max()))
+
+
+def test_forward_dc_c2_full_grid(api, oracle_mod):
+    """The same check on the c2 system itself: the full 128^3 grid at 0.1 mm,
+    the 128-element cylindrical array at U 11, dl 11, eight positions from
+    two rotation angles (elements near both ends and the middle of the
+    array), x with 12 seeded voxels anywhere in the grid."""
+    w = W.c2(angles=[0.0, 37 * 2 * math.pi / 180], with_x=False)
+    w = w.with_tx(w.tx[[3, 50, 90, 127, 128 + 10, 128 + 64, 128 + 100, 128 + 121]])
+    w = _sparse(w, 12, seed=21)
+    eps = _safe_eps(oracle_mod, w)
+    x32 = w.x.astype(np.float32)
+    plan = api.Plan(w, taps=oracle_mod.taps_for(w))
+    ds = plan.forward_dc(torch.from_numpy(x32).cuda()).cpu().numpy()
+    x64 = x32.astype(np.float64)
+    fd = (_oracle_s(oracle_mod, w, w.c + eps, x64) - _oracle_s(oracle_mod, w, w.c - eps, x64)) / (2 * eps)
+    e = rel(ds, fd)
+    print(f"c2 full grid eps={eps:.2e} rel L2 {e:.3e}")
+    assert e <= DC_TOL[("cylinder", 11)], e
