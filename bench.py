@@ -328,6 +328,13 @@ def conv_all_rows(api, taps, dev):
     v_plain = plan.conv_adjoint(s_plain)
     v_tc = tc.conv_adjoint(s_plain)
     t_tc = cuda_ms(lambda: tc.conv_forward(f), reps=3)
+    # the split-plane kernel pat_forward uses: f as BF16 hi and lo planes (the
+    # epilogue's output format), brought into the tensor cores by tensor-map copies
+    planes = tc.conv_split(f)
+    s_sp = tc.conv_forward_split(planes)
+    t_sp = cuda_ms(lambda: tc.conv_forward_split(planes), reps=5)
+    sp_bytes = 2 * 2 * w.K * w.UL + 4 * w.K * w.L  # planes read once, s written
+    hbm = measured_hbm_gbs()
     nw = w.T + w.U - 1
     kw = -(-(127 * w.U + nw) // 64) * 64  # Toeplitz contraction length per 128-sample tile
     flops = 3 * 2 * 128 * 64 * kw * (-(-w.L // 128)) * (-(-w.K // 64))
@@ -337,8 +344,23 @@ def conv_all_rows(api, taps, dev):
                           "tcgen05_bf16x3": cuda_ms(lambda: tc.conv_adjoint(s_plain), reps=3)},
            "rel_l2_tc_vs_fp64": {"forward": rel_l2(s_tc, s_plain), "adjoint": rel_l2(v_tc, v_plain)},
            "tcgen05_forward_tflops": flops / (t_tc * 1e-3) / 1e12,
+           "split_plane_forward": {"ms": t_sp, "rel_l2_vs_fp64": rel_l2(s_sp, s_plain),
+                                   "bytes": sp_bytes, "gb_per_s": sp_bytes / (t_sp * 1e-3) / 1e9,
+                                   "hbm_peak_gb_per_s": hbm,
+                                   "frac_of_hbm": (sp_bytes / (t_sp * 1e-3) / 1e9) / hbm if hbm else None,
+                                   "method_tflops": 2.0 * w.K * w.L * nw / (t_sp * 1e-3) / 1e12,
+                                   "tiles": (-(-w.L // 128)) * (-(-w.K // 256))},
            "tc_error": api._lib.pat_plan_get_info(tc.handle)["tc_error"]}
     return out
+
+
+def measured_hbm_gbs():
+    """The HBM copy bandwidth of this GPU pool (MEASURED_PEAKS.json), else the
+    6.8 TB/s fallback of one earlier GB300 measurement."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        return 6800.0
 
 
 def fista_compare(api, dev, first, n_prob, iters, power):

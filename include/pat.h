@@ -80,7 +80,8 @@ enum { PAT_EIR_GAUSS_SINE = 0, PAT_EIR_BOX = 1 };
  *                        row (Eq. plane_decomp_u); planar elements are kept.
  *                        pat_plan_info counts pairs and windows per plane. */
 enum { PAT_FLAG_ALLOW_CLIP = 1, PAT_FLAG_CONV_TC = 2, PAT_FLAG_PIECEWISE_PLANES = 4 };
-enum { PAT_OP_FORWARD = 1, PAT_OP_ADJOINT = 2, PAT_OP_RECON = 3, PAT_OP_FORWARD_DC = 4, PAT_OP_AUTOTUNE = 5 };
+enum { PAT_OP_FORWARD = 1, PAT_OP_ADJOINT = 2, PAT_OP_RECON = 3, PAT_OP_FORWARD_DC = 4, PAT_OP_AUTOTUNE = 5,
+       PAT_OP_CONV_SPLIT = 6 };
 
 /* Uniform voxel grid (Sec. 2.4): centres origin + pitch * (ix, iy, iz). */
 typedef struct pat_grid {
@@ -196,8 +197,9 @@ pat_status pat_plan_destroy(pat_plan *plan);
 /* Plan facts (see pat_plan_info). */
 pat_status pat_plan_get_info(const pat_plan *plan, pat_plan_info *info);
 
-/* Workspace bytes needed by op (PAT_OP_FORWARD, PAT_OP_ADJOINT, PAT_OP_RECON);
- * 0 for a null plan or unknown op. */
+/* Workspace bytes needed by op (PAT_OP_FORWARD, PAT_OP_ADJOINT, PAT_OP_RECON,
+ * PAT_OP_FORWARD_DC, PAT_OP_AUTOTUNE; PAT_OP_CONV_SPLIT: the planes of
+ * pat_conv_split); 0 for a null plan or unknown op. */
 size_t pat_workspace_bytes(const pat_plan *plan, int32_t op);
 
 /* s = A x (Alg. 1): x device float[N], s device float[K][L] (overwritten).
@@ -218,6 +220,19 @@ pat_status pat_forward_geometric(pat_plan *plan, const float *x, float *f, void 
 pat_status pat_conv_forward(pat_plan *plan, const float *f, float *s, void *stream);
 /* v[K][U L] = h-bar^- * upsample_U^T(s) (App. G) from s[K][L]. */
 pat_status pat_conv_adjoint(pat_plan *plan, const float *s, float *v, void *stream);
+/* Tensor-core plans (PAT_FLAG_CONV_TC) only, else PAT_ERR_UNSUPPORTED: the
+ * convolution of Eq. (discrete_conv) from f in the split form pat_forward
+ * uses inside.  pat_conv_split writes f[K][U L] (device floats) as two BF16
+ * planes, hi = bf16(f) then lo = bf16(f - hi), each [K][ld] with ld = U L
+ * rounded up to a multiple of 8, into planes (device uint16, 16-byte
+ * aligned, pat_workspace_bytes(plan, PAT_OP_CONV_SPLIT) bytes; the padding
+ * columns are zero).  pat_conv_forward_split computes s[K][L] (device
+ * floats, overwritten) from such planes with the persistent tensor-map /
+ * tcgen05 kernel (only the first U L columns of each row are read).  Both
+ * are asynchronous on stream; a wait that gave up on the device shows in
+ * pat_plan_info.tc_error. */
+pat_status pat_conv_split(pat_plan *plan, const float *f, uint16_t *planes, void *stream);
+pat_status pat_conv_forward_split(pat_plan *plan, const uint16_t *planes, float *s, void *stream);
 /* z[N] = transpose of the geometric assembly applied to v[K][U L] (Alg. 7 / Alg. 6). */
 pat_status pat_adjoint_geometric(pat_plan *plan, const float *v, float *z, void *ws, size_t ws_bytes, void *stream);
 

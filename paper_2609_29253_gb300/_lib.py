@@ -17,7 +17,7 @@ from . import build as _build
 
 PAT_OK = 0
 PAT_ERR_WORKSPACE = 4
-PAT_OP_FORWARD, PAT_OP_ADJOINT, PAT_OP_RECON, PAT_OP_FORWARD_DC, PAT_OP_AUTOTUNE = 1, 2, 3, 4, 5
+PAT_OP_FORWARD, PAT_OP_ADJOINT, PAT_OP_RECON, PAT_OP_FORWARD_DC, PAT_OP_AUTOTUNE, PAT_OP_CONV_SPLIT = 1, 2, 3, 4, 5, 6
 PAT_FLAG_ALLOW_CLIP = 1
 PAT_FLAG_CONV_TC = 2
 PAT_FLAG_PIECEWISE_PLANES = 4
@@ -59,7 +59,7 @@ class pat_plan_info(C.Structure):
 
 EXPORTS = ["pat_system_kernel", "pat_system_kernel_dc", "pat_plan_create", "pat_plan_destroy", "pat_plan_get_info",
            "pat_workspace_bytes", "pat_forward", "pat_adjoint", "pat_forward_geometric", "pat_conv_forward",
-           "pat_conv_adjoint", "pat_adjoint_geometric", "pat_forward_dc", "pat_recon", "pat_recon_batch",
+           "pat_conv_adjoint", "pat_conv_split", "pat_conv_forward_split", "pat_adjoint_geometric", "pat_forward_dc", "pat_recon", "pat_recon_batch",
            "pat_plan_autotune", "pat_forward_static", "pat_measure_peaks", "pat_last_error", "pat_version"]
 
 _lock = threading.Lock()
@@ -100,7 +100,7 @@ def load(build_if_missing: bool = True):
         for nm in ("pat_forward", "pat_adjoint", "pat_forward_geometric", "pat_adjoint_geometric"):
             getattr(L, nm).restype = st
             getattr(L, nm).argtypes = [vp, vp, vp, vp, C.c_size_t, vp]
-        for nm in ("pat_conv_forward", "pat_conv_adjoint"):
+        for nm in ("pat_conv_forward", "pat_conv_adjoint", "pat_conv_split", "pat_conv_forward_split"):
             getattr(L, nm).restype = st
             getattr(L, nm).argtypes = [vp, vp, vp, vp]
         L.pat_forward_static.restype = st
@@ -208,6 +208,14 @@ def pat_conv_forward(plan, f, s, stream=None):
 
 def pat_conv_adjoint(plan, s, v, stream=None):
     check(load().pat_conv_adjoint(plan, _ptr(s), _ptr(v), _stream(stream)))
+
+
+def pat_conv_split(plan, f, planes, stream=None):
+    check(load().pat_conv_split(plan, _ptr(f), _ptr(planes), _stream(stream)))
+
+
+def pat_conv_forward_split(plan, planes, s, stream=None):
+    check(load().pat_conv_forward_split(plan, _ptr(planes), _ptr(s), _stream(stream)))
 
 
 def pat_recon(plan, s, x, iters, lambda_R, step, ws, stream=None):

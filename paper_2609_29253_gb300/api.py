@@ -104,6 +104,21 @@ class Plan:
         _lib.pat_conv_forward(self.handle, f, s)
         return s
 
+    def conv_split(self, f: torch.Tensor) -> torch.Tensor:
+        """f [K][U L] as the BF16 hi and lo planes of pat_conv_split (int16
+        storage, [2][K][ld]; tensor-core plans only)."""
+        f = self._f32(f, self.K * self.UL)
+        n = _lib.pat_workspace_bytes(self.handle, _lib.PAT_OP_CONV_SPLIT) // 2
+        planes = torch.empty(n, dtype=torch.int16, device=self.device)
+        _lib.pat_conv_split(self.handle, f, planes)
+        return planes
+
+    def conv_forward_split(self, planes: torch.Tensor) -> torch.Tensor:
+        """s [K][L] from the planes of conv_split (pat_conv_forward_split)."""
+        s = torch.empty((self.K, self.L), dtype=torch.float32, device=self.device)
+        _lib.pat_conv_forward_split(self.handle, planes, s)
+        return s
+
     def conv_adjoint(self, s: torch.Tensor) -> torch.Tensor:
         s = self._f32(s, self.K * self.L)
         v = torch.empty((self.K, self.UL), dtype=torch.float32, device=self.device)

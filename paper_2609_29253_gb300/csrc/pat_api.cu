@@ -40,7 +40,7 @@ struct pat_plan {
     // PAT_FLAG_CONV_TC: tensor-core convolution tables and error word
     bool tc;
     TcGeometry tcg;
-    uint8_t *tc_fwd_tab, *tc_adj_tab;
+    uint8_t *tc_fwd_tab, *tc_adj_tab, *tc_fwd2_tab; // FP32-input forward, adjoint, split-plane forward
     int *tc_err;
     // PAT_METHOD_LUT: the tables of E~ and F~ with their node arrays (one allocation)
     void *lut_buf;
@@ -269,10 +269,11 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
     p->tc = (params->flags & PAT_FLAG_CONV_TC) != 0;
     if (p->tc) {
         p->tcg = tc_geometry(n_taps, params->U, params->L, n_lo);
-        if (p->tcg.fwd_smem > (size_t)optin || p->tcg.adj_smem > (size_t)optin) {
+        const size_t need_tc = std::max(std::max(p->tcg.fwd_smem, p->tcg.adj_smem), p->tcg.fwd2_smem);
+        if (need_tc > (size_t)optin) {
             delete p;
             return fail(PAT_ERR_UNSUPPORTED, "tensor-core convolution needs %zu bytes of shared memory per block, "
-                        "device has %d", std::max(p->tcg.fwd_smem, p->tcg.adj_smem), optin);
+                        "device has %d", need_tc, optin);
         }
     }
     size_t need_epi = sizeof(float) * (size_t)(tm.UL + p->nW) + 64;
@@ -332,12 +333,14 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
         if (p->tc) {
             if (cudaMalloc(&p->tc_fwd_tab, p->tcg.fwd_table_bytes) != cudaSuccess ||
                 cudaMalloc(&p->tc_adj_tab, p->tcg.adj_table_bytes) != cudaSuccess ||
+                cudaMalloc(&p->tc_fwd2_tab, p->tcg.fwd2_table_bytes) != cudaSuccess ||
                 cudaMalloc(&p->tc_err, sizeof(int)) != cudaSuccess) {
                 rc = fail(PAT_ERR_CUDA, "pat_plan_create: cudaMalloc failed");
                 break;
             }
             if (cudaMemsetAsync(p->tc_err, 0, sizeof(int), s) != cudaSuccess ||
-                launch_tc_tables(p->taps, n_taps, params->U, p->tcg, p->tc_fwd_tab, p->tc_adj_tab, s) != cudaSuccess) {
+                launch_tc_tables(p->taps, n_taps, params->U, p->tcg, p->tc_fwd_tab, p->tc_adj_tab, p->tc_fwd2_tab, s) !=
+                    cudaSuccess) {
                 rc = fail(PAT_ERR_CUDA, "pat_plan_create: tensor-core tables failed");
                 break;
             }
@@ -466,6 +469,7 @@ extern "C" pat_status pat_plan_destroy(pat_plan *p)
     cudaFree(p->scal);
     cudaFree(p->tc_fwd_tab);
     cudaFree(p->tc_adj_tab);
+    cudaFree(p->tc_fwd2_tab);
     cudaFree(p->tc_err);
     cudaFree(p->lut_buf);
     cudaSetDevice(cur);
@@ -491,11 +495,13 @@ extern "C" pat_status pat_plan_get_info(const pat_plan *p, pat_plan_info *info)
 }
 
 // forward: difference array D [K][UL + 1] doubles, then (tensor-core
-// convolution) f [K][UL] floats; adjoint: prefix sums P [K][UL + 1] float2,
-// then (tensor-core convolution) v [K][UL] floats
+// convolution) f as BF16 hi and lo planes [K][ld] each, ld = UL rounded up
+// to a multiple of 8; adjoint: prefix sums P [K][UL + 1] float2, then
+// (tensor-core convolution) v [K][UL] floats in the same place
 static size_t ws_D(const pat_plan *p) { return align256(sizeof(double) * (size_t)(p->tm.UL + 1) * p->K); }
 static size_t ws_P(const pat_plan *p) { return align256(sizeof(float2) * (size_t)(p->tm.UL + 1) * p->K); }
-static size_t ws_f(const pat_plan *p) { return p->tc ? align256(sizeof(float) * (size_t)p->tm.UL * p->K) : 0; }
+static size_t ws_planes(const pat_plan *p) { return align256(2 * sizeof(uint16_t) * (size_t)p->tcg.ld * p->K); }
+static size_t ws_f(const pat_plan *p) { return p->tc ? ws_planes(p) : 0; }
 static size_t ws_fwd(const pat_plan *p) { return ws_D(p) + ws_f(p); }
 static size_t ws_adj(const pat_plan *p) { return ws_P(p) + ws_f(p); }
 static size_t ws_fwd_dc(const pat_plan *p) { return 2 * ws_D(p); }
@@ -515,6 +521,7 @@ extern "C" size_t pat_workspace_bytes(const pat_plan *p, int32_t op)
     if (op == PAT_OP_RECON) return ws_recon(p);
     if (op == PAT_OP_FORWARD_DC) return ws_fwd_dc(p);
     if (op == PAT_OP_AUTOTUNE) return ws_tune(p);
+    if (op == PAT_OP_CONV_SPLIT) return p->tc ? ws_planes(p) : 0;
     return 0;
 }
 
@@ -537,9 +544,12 @@ static pat_status enqueue_forward(pat_plan *p, const float *x, float *s, float *
                        st));
     int mode = p->tm.method == PAT_METHOD_POINT ? 1 : 0;
     if (p->tc && s) {
-        float *fw = (float *)((char *)ws + ws_D(p));
-        CK(launch_fwd_epilogue(D, p->tm.UL + 1, p->W, p->nW, p->n_lo, p->tm, mode, p->K, nullptr, fw, st));
-        CK(launch_conv_tc_fwd(fw, p->tc_fwd_tab, p->tcg, p->K, p->tm.L, p->tm.U, s, p->tc_err, st));
+        // f leaves the epilogue as BF16 hi and lo planes, which the tensor-core
+        // kernel's copy engine brings straight into the operand layout
+        uint16_t *hi = (uint16_t *)((char *)ws + ws_D(p)), *lo = hi + (size_t)p->tcg.ld * p->K;
+        CK(launch_fwd_epilogue(D, p->tm.UL + 1, p->W, p->nW, p->n_lo, p->tm, mode, p->K, nullptr, nullptr, st, hi, lo,
+                               p->tcg.ld));
+        CK(launch_conv_tc_fwd2(hi, lo, p->tc_fwd2_tab, p->tcg, p->K, p->tm.L, p->tm.U, s, p->tc_err, st));
         return PAT_OK;
     }
     CK(launch_fwd_epilogue(D, p->tm.UL + 1, p->W, p->nW, p->n_lo, p->tm, mode, p->K, s, f, st));
@@ -589,6 +599,29 @@ extern "C" pat_status pat_conv_forward(pat_plan *p, const float *f, float *s, vo
         return PAT_OK;
     }
     CK(launch_fwd_epilogue(f, p->tm.UL, p->W, p->nW, p->n_lo, p->tm, 2, p->K, s, nullptr, (cudaStream_t)stream));
+    return PAT_OK;
+}
+
+extern "C" pat_status pat_conv_split(pat_plan *p, const float *f, uint16_t *planes, void *stream)
+{
+    g_err.clear();
+    if (!p || !f || !planes) return fail(PAT_ERR_INVALID_ARG, "pat_conv_split: null pointer");
+    if (!p->tc) return fail(PAT_ERR_UNSUPPORTED, "pat_conv_split: the plan has no tensor-core convolution");
+    if (((uintptr_t)planes & 15) != 0) return fail(PAT_ERR_INVALID_ARG, "pat_conv_split: planes must be 16-byte aligned");
+    CK(launch_split_bf16(f, p->K, p->tm.UL, p->tcg.ld, planes, planes + (size_t)p->tcg.ld * p->K,
+                         (cudaStream_t)stream));
+    return PAT_OK;
+}
+
+extern "C" pat_status pat_conv_forward_split(pat_plan *p, const uint16_t *planes, float *s, void *stream)
+{
+    g_err.clear();
+    if (!p || !planes || !s) return fail(PAT_ERR_INVALID_ARG, "pat_conv_forward_split: null pointer");
+    if (!p->tc) return fail(PAT_ERR_UNSUPPORTED, "pat_conv_forward_split: the plan has no tensor-core convolution");
+    if (((uintptr_t)planes & 15) != 0)
+        return fail(PAT_ERR_INVALID_ARG, "pat_conv_forward_split: planes must be 16-byte aligned");
+    CK(launch_conv_tc_fwd2(planes, planes + (size_t)p->tcg.ld * p->K, p->tc_fwd2_tab, p->tcg, p->K, p->tm.L, p->tm.U, s,
+                           p->tc_err, (cudaStream_t)stream));
     return PAT_OK;
 }
 
@@ -960,7 +993,8 @@ extern "C" pat_status pat_forward_static(pat_plan *p, const float *x, float *s, 
         return fail(PAT_ERR_WORKSPACE,
                     "pat_forward_static: this plan needs %zu bytes of scratch (%s), the fixed array holds %u; "
                     "use pat_forward with a caller workspace",
-                    need, p->tc ? "K (U L + 1) 8 + K U L 4 bytes" : "K (U L + 1) 8 bytes",
+                    need, p->tc ? "K (U L + 1) 8 + K ld 4 bytes, ld = U L rounded up to a multiple of 8"
+                                : "K (U L + 1) 8 bytes",
                     (unsigned)PAT_STATIC_SCRATCH_BYTES);
     int dev = 0;
     CK(cudaGetDevice(&dev));

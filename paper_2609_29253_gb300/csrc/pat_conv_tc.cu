@@ -40,6 +40,7 @@
 // an error and returns before touching the tensor cores).  Every wait is
 // bounded: after about two seconds the CTA records an error code, finishes
 // what it issued and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -653,6 +654,264 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_adj_kernel(const float *__
 }
 
 // ---------------------------------------------------------------------------
+// Forward from split planes: s from f given as two BF16 planes (hi, lo) of
+// [K][ld] elements (ld a multiple of 8), persistent CTAs, one per SM.
+//
+// Tile: 128 output samples x 256 transducers (M 128, N 256: one MMA keeps
+// the tensor cores at their full rate, where N = 64 ran them at about a
+// third).  Stage: 64 fine bins of the window, T (hi, lo) from the table by
+// one bulk copy and B (hi, lo) by two tensor-map copies (TMA) that land in
+// the 128-byte swizzle layout of the operand descriptor, so no thread
+// touches f: the kernel is a copy engine feeding the tensor cores.  The
+// window of output tile l0 starts at U l0 + m0a with m0a = m0off - shift a
+// multiple of 8 (the table's leading `shift` columns are zero), so every
+// tensor-map x coordinate is a multiple of 8 BF16 elements (16 bytes); the
+// coordinates outside [0, U L) and the rows beyond K read the copy engine's
+// zero fill.
+//
+// Warp roles: warp 0 (lane 0) issues the copies into a ring of two stage
+// slots; warp 1 (lane 0) issues 3 x 4 MMAs per stage into one of two TMEM
+// accumulators of 256 columns, alternating between tiles, and commits each
+// stage onto the slot's `empty` barrier and each tile onto the accumulator's
+// `tfull`; warps 2-5 read a finished accumulator (each warp the TMEM lanes
+// of its rank within the warp group), store the tile into s and arrive on
+// `tempty`, so that the MMAs of the next tile overlap the store.  Every wait
+// is bounded (about 2 s, or as soon as another thread has given up); a
+// thread that gives up records an error, waits (bounded) for what it issued
+// and leaves.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kN2 = kTcN2, kRing2 = 2;
+constexpr int kB2Half = kN2 * kKS * 2;            // bytes of one B plane stage
+constexpr int kSlot2 = 2 * kAHalf + 2 * kB2Half; // T hi, T lo, B hi, B lo
+constexpr uint32_t kIdesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN2 >> 3) << 17) |
+                             ((uint32_t)(kM >> 4) << 24);
+static_assert(kTcThreadsFwd2 == 192, "copy warp, MMA warp, four epilogue warps");
+
+__device__ __forceinline__ void mma_bf16_n256(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t accumulate)
+{
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "setp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+                 "l"(a), "l"(b), "r"(kIdesc2), "r"(accumulate)
+                 : "memory");
+}
+
+// 2-D tensor-map copy of one box into shared memory, completing on bar.
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                 "[%4];" ::"r"(dst),
+                 "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+                 : "memory");
+}
+
+struct Fwd2 {
+    uint8_t *slot[kRing2];
+    uint32_t full[kRing2], empty[kRing2], tfull[2], tempty[2];
+    uint32_t *tslot;
+    int *abort_flag;
+};
+
+__device__ __forceinline__ Fwd2 carve_fwd2(uint8_t *base)
+{
+    Fwd2 r;
+    for (int i = 0; i < kRing2; ++i) r.slot[i] = base + (size_t)i * kSlot2;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + (size_t)kRing2 * kSlot2);
+    for (int i = 0; i < kRing2; ++i) {
+        r.full[i] = smem_u32(&bars[i]);
+        r.empty[i] = smem_u32(&bars[kRing2 + i]);
+    }
+    for (int i = 0; i < 2; ++i) {
+        r.tfull[i] = smem_u32(&bars[2 * kRing2 + i]);
+        r.tempty[i] = smem_u32(&bars[2 * kRing2 + 2 + i]);
+    }
+    r.tslot = reinterpret_cast<uint32_t *>(&bars[2 * kRing2 + 4]);
+    r.abort_flag = reinterpret_cast<int *>(&bars[2 * kRing2 + 5]);
+    return r;
+}
+
+__device__ __forceinline__ bool fwd2_wait(const Fwd2 &R, uint32_t bar, uint32_t parity)
+{
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity)) {
+        if (*(volatile int *)R.abort_flag) return false;
+        __nanosleep(32);
+        if (clock64() - t0 > kSpinCycles) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void fwd2_abort(const Fwd2 &R, int *err, int code)
+{
+    *(volatile int *)R.abort_flag = 1;
+    atomicExch(err, code);
+}
+
+} // namespace
+
+__global__ void __launch_bounds__(kTcThreadsFwd2, 1)
+    conv_tc_fwd2_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
+                        const uint8_t *__restrict__ Tf, int nst, int m0a, int K, int L, int U,
+                        float *__restrict__ s, int *__restrict__ err)
+{
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    if (smem_u32(smem_raw) & 1023u) { // swizzled operand tiles need 1024-byte alignment
+        if (threadIdx.x == 0) atomicExch(err, 6);
+        return;
+    }
+    const Fwd2 R = carve_fwd2(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kRing2; ++i) {
+            mbar_init(R.full[i], 1);
+            mbar_init(R.empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(R.tfull[i], 1);
+            mbar_init(R.tempty[i], 4);
+        }
+        *R.abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    if (warp == 0) { // two accumulators of kN2 FP32 columns
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(R.tslot)),
+                     "r"((uint32_t)(2 * kN2))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *R.tslot;
+    const int nlt = (L + kM - 1) / kM, nkt = (K + kN2 - 1) / kN2, ntiles = nlt * nkt;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // copies: stage g of this CTA into slot g % 2 once the MMAs of stage g - 2 are done
+            int g = 0;
+            bool ok = (m0a & 7) == 0;
+            if (!ok) fwd2_abort(R, err, 7);
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int l0 = (t % nlt) * kM, k0 = (t / nlt) * kN2;
+                const int x0 = U * l0 + m0a;
+                for (int st = 0; st < nst; ++st, ++g) {
+                    const int b = g & 1;
+                    if (g >= kRing2 && !fwd2_wait(R, R.empty[b], ((g >> 1) - 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *sl = R.slot[b];
+                    mbar_expect_tx(R.full[b], (uint32_t)kSlot2);
+                    bulk_g2s(smem_u32(sl), Tf + (size_t)st * 2 * kAHalf, 2 * kAHalf, R.full[b]);
+                    tma_2d(smem_u32(sl + 2 * kAHalf), &map_hi, x0 + st * kKS, k0, R.full[b]);
+                    tma_2d(smem_u32(sl + 2 * kAHalf + kB2Half), &map_lo, x0 + st * kKS, k0, R.full[b]);
+                }
+            }
+            if (!ok) {
+                fwd2_abort(R, err, 8);
+                // bounded waits for the copies still in flight: at most the last
+                // two stages, each its slot's latest phase
+                for (int q = g > kRing2 ? g - kRing2 : 0; q < g; ++q) mbar_wait(R.full[q & 1], (q >> 1) & 1);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int g = 0, ti = 0, last_commit = -1;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++ti) {
+                const int a = ti & 1;
+                if (ti >= 2 && !fwd2_wait(R, R.tempty[a], ((ti >> 1) - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t td = tmem + (uint32_t)(a * kN2);
+                for (int st = 0; st < nst; ++st, ++g) {
+                    const int b = g & 1;
+                    if (!fwd2_wait(R, R.full[b], (g >> 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint8_t *sl = R.slot[b];
+                    const uint32_t ahi = smem_u32(sl), alo = ahi + kAHalf, bh = ahi + 2 * kAHalf, bl = bh + kB2Half;
+#pragma unroll
+                    for (int ks = 0; ks < kKS / 16; ++ks) {
+                        const uint32_t o = ks * 32;
+                        mma_bf16_n256(td, sdesc(ahi + o), sdesc(bh + o), (st == 0 && ks == 0) ? 0u : 1u);
+                        mma_bf16_n256(td, sdesc(ahi + o), sdesc(bl + o), 1u);
+                        mma_bf16_n256(td, sdesc(alo + o), sdesc(bh + o), 1u);
+                    }
+                    mma_commit(R.empty[b]);
+                    last_commit = g;
+                }
+                if (ok) mma_commit(R.tfull[a]);
+            }
+            if (!ok) {
+                fwd2_abort(R, err, 9);
+                if (last_commit >= 0) mbar_wait(R.empty[last_commit & 1], (last_commit >> 1) & 1);
+            }
+        }
+    } else {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (output samples)
+        const int q4 = warp & 3;
+        int ti = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++ti) {
+            const int a = ti & 1;
+            int ok = 0;
+            if (lane == 0) ok = fwd2_wait(R, R.tfull[a], (ti >> 1) & 1) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                if (lane == 0) fwd2_abort(R, err, 10);
+                break;
+            }
+            fence_after();
+            const int l0 = (t % nlt) * kM, k0 = (t / nlt) * kN2;
+            const int l = l0 + q4 * 32 + lane;
+#pragma unroll 1
+            for (int c = 0; c < kN2; c += 16) {
+                float r[16];
+                tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(a * kN2 + c), r);
+                if (l < L) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int k = k0 + c + j;
+                        if (k < K) s[(long long)k * L + l] = r[j];
+                    }
+                }
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(R.tempty[a]);
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * kN2))
+                     : "memory");
+}
+
+// f [K][UL] floats -> hi, lo planes [K][ld] (the split of build_b; the
+// padding columns are zero).
+__global__ void split_bf16_kernel(const float *__restrict__ f, int K, int UL, int ld, uint16_t *__restrict__ hi,
+                                  uint16_t *__restrict__ lo)
+{
+    const long long n = (long long)K * ld;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e / ld), m = (int)(e % ld);
+        const float v = m < UL ? f[(long long)k * UL + m] : 0.f;
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+        hi[e] = __bfloat16_as_ushort(h);
+        lo[e] = __bfloat16_as_ushort(l);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Operand tables (plan set-up, FP64 taps -> BF16 hi / lo in the operand layout)
 // ---------------------------------------------------------------------------
 // W[j] = (1/U) sum_{u<U} h-bar[j - (U-1) + u] in FP64
@@ -676,14 +935,16 @@ __device__ __forceinline__ void put_split(uint8_t *stage, int row, int kk, doubl
     *reinterpret_cast<__nv_bfloat16 *>(stage + kAHalf + off) = lo;
 }
 
-// Tf[st]: element (i, kk) = W[U i + nW - 1 - (st kKS + kk)]
-__global__ void tc_table_fwd_kernel(const double *__restrict__ taps, int T, int U, int nst, uint8_t *__restrict__ Tf)
+// Tf[st]: element (i, kk) = W[U i + nW - 1 - (st kKS + kk - shift)] (zero for
+// the shift's leading columns: a window that starts shift bins early)
+__global__ void tc_table_fwd_kernel(const double *__restrict__ taps, int T, int U, int nst, int shift,
+                                    uint8_t *__restrict__ Tf)
 {
     const long long n = (long long)nst * kM * kKS;
     const int nW = T + U - 1;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         const int st = (int)(e / (kM * kKS)), r = (int)(e % (kM * kKS)), i = r / kKS, kk = r % kKS;
-        const int mu = st * kKS + kk;
+        const int mu = st * kKS + kk - shift;
         put_split(Tf + (size_t)st * 2 * kAHalf, i, kk, w64(taps, T, U, U * i + nW - 1 - mu));
     }
 }
@@ -734,15 +995,83 @@ TcGeometry tc_geometry(int T, int U, int L, int n_lo)
                                                   cudaSuccess)
         g.sms = 1;
     g.adj_smem = 4 * kAHalf + (size_t)g.nst_adj * 2 * kBHalf + 64;
-    (void)L;
+    // split-plane forward: window start shifted down to a multiple of 8 fine bins
+    g.shift = ((g.m0off % 8) + 8) % 8;
+    g.m0a = g.m0off - g.shift;
+    g.nst_fwd2 = (kw + g.shift + kKS - 1) / kKS;
+    g.fwd2_table_bytes = (size_t)g.nst_fwd2 * 2 * kAHalf;
+    g.fwd2_smem = (size_t)kRing2 * kSlot2 + 8 * (2 * kRing2 + 6) + 1024;
+    g.ld = (U * L + 7) / 8 * 8;
     return g;
 }
 
 cudaError_t launch_tc_tables(const double *taps, int T, int U, const TcGeometry &g, uint8_t *Tf, uint8_t *Ta,
-                             cudaStream_t st)
+                             uint8_t *Tf2, cudaStream_t st)
 {
-    tc_table_fwd_kernel<<<304, 256, 0, st>>>(taps, T, U, g.nst_fwd, Tf);
+    tc_table_fwd_kernel<<<304, 256, 0, st>>>(taps, T, U, g.nst_fwd, 0, Tf);
     tc_table_adj_kernel<<<608, 256, 0, st>>>(taps, T, U, g.nst_adj, g.d0, g.c, Ta);
+    tc_table_fwd_kernel<<<304, 256, 0, st>>>(taps, T, U, g.nst_fwd2, g.shift, Tf2);
+    return cudaGetLastError();
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once (the library links
+// the runtime statically and not the driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        looked = true;
+    }
+    return fn;
+}
+
+// Tensor map of one BF16 plane [K][ld]: boxes of 64 fine bins (128 bytes, the
+// swizzle span) x 256 rows, 128-byte swizzle, zero fill outside.
+static cudaError_t plane_map(CUtensorMap *m, const uint16_t *plane, int K, int UL, int ld)
+{
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn) return cudaErrorNotSupported;
+    if (((uintptr_t)plane & 15) != 0 || (ld % 8) != 0 || UL > ld) return cudaErrorInvalidValue;
+    // extent U L: the row padding [U L, ld) reads as zero fill, like every column outside
+    const cuuint64_t dims[2] = {(cuuint64_t)UL, (cuuint64_t)K};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kKS, (cuuint32_t)kN2};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)plane, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_split_bf16(const float *f, int K, int UL, int ld, uint16_t *hi, uint16_t *lo, cudaStream_t st)
+{
+    split_bf16_kernel<<<1216, 256, 0, st>>>(f, K, UL, ld, hi, lo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_conv_tc_fwd2(const uint16_t *hi, const uint16_t *lo, const uint8_t *Tf2, const TcGeometry &g, int K,
+                                int L, int U, float *s, int *err, cudaStream_t st)
+{
+    CUtensorMap mh, ml;
+    cudaError_t e = plane_map(&mh, hi, K, U * L, g.ld);
+    if (e == cudaSuccess) e = plane_map(&ml, lo, K, U * L, g.ld);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute((const void *)conv_tc_fwd2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)g.fwd2_smem);
+    if (e != cudaSuccess) return e;
+    const int ntiles = ((L + kM - 1) / kM) * ((K + kN2 - 1) / kN2);
+    const unsigned grid = (unsigned)std::max(1, std::min(ntiles, g.sms));
+    conv_tc_fwd2_kernel<<<grid, kTcThreadsFwd2, g.fwd2_smem, st>>>(mh, ml, Tf2, g.nst_fwd2, g.m0a, K, L, U, s, err);
     return cudaGetLastError();
 }
 

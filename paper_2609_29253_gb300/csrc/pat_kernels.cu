@@ -15,6 +15,8 @@
 //                        4x4x2 voxels, loop over all transducers, no write
 //                        conflicts (App. G)
 //   taps_kernel          discrete system kernel h-bar (Eq. def_bh), FP64
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cstdio>
 
@@ -498,7 +500,8 @@ __device__ __forceinline__ void conv_down(const float *f, const float *W, int nW
 __global__ void __launch_bounds__(kThreads) fwd_epilogue_kernel(const void *__restrict__ in, int in_stride,
                                                                  const float *__restrict__ Wg, int nW, int n_lo,
                                                                  TimeDev tm, int mode, float *__restrict__ s,
-                                                                 float *__restrict__ f_out)
+                                                                 float *__restrict__ f_out, uint16_t *__restrict__ f_hi,
+                                                                 uint16_t *__restrict__ f_lo, int ld)
 {
     extern __shared__ float sm[];
     __shared__ double tmp[kWarpsPerBlock];
@@ -528,6 +531,14 @@ __global__ void __launch_bounds__(kThreads) fwd_epilogue_kernel(const void *__re
     if (f_out) {
         float *fo = f_out + (size_t)k * UL;
         for (int b = threadIdx.x; b < UL; b += blockDim.x) fo[b] = f[b];
+    }
+    if (f_hi) { // f split into BF16 planes for the tensor-core convolution: hi = bf16(f), lo = bf16(f - hi)
+        uint16_t *ho = f_hi + (size_t)k * ld, *lo = f_lo + (size_t)k * ld;
+        for (int b = threadIdx.x; b < UL; b += blockDim.x) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(f[b]);
+            ho[b] = __bfloat16_as_ushort(h);
+            lo[b] = __bfloat16_as_ushort(__float2bfloat16_rn(f[b] - __bfloat162float(h)));
+        }
     }
     if (s) conv_down(f, W, nW, n_lo, tm, s + (size_t)k * tm.L);
 }
@@ -1066,11 +1077,12 @@ cudaError_t launch_fwd_dc_epilogue(const double *Dg, const double *Dd, const flo
 }
 
 cudaError_t launch_fwd_epilogue(const void *in, int in_stride, const float *W, int nW, int n_lo, const TimeDev &tm,
-                                int mode, int K, float *s, float *f_out, cudaStream_t st)
+                                int mode, int K, float *s, float *f_out, cudaStream_t st, uint16_t *f_hi,
+                                uint16_t *f_lo, int ld)
 {
     size_t smem = sizeof(float) * (size_t)(tm.UL + nW);
     set_smem_attr((const void *)fwd_epilogue_kernel, smem);
-    fwd_epilogue_kernel<<<K, kThreads, smem, st>>>(in, in_stride, W, nW, n_lo, tm, mode, s, f_out);
+    fwd_epilogue_kernel<<<K, kThreads, smem, st>>>(in, in_stride, W, nW, n_lo, tm, mode, s, f_out, f_hi, f_lo, ld);
     return cudaGetLastError();
 }
 

@@ -30,9 +30,11 @@ cudaError_t launch_scan(const TxDev *tx, int K, const TimeDev &tm, const GridDev
 // rows[k] (Kf == K: one element per row).
 cudaError_t launch_fwd_geom(const TxDev *tx, int Kf, int K, const int *rows, int kind, const TimeDev &tm,
                             const GridDev &g, const float *x, double *Dg, int bpc, int span, cudaStream_t st);
-// in: doubles for mode 0 / 1 (difference array, histogram), floats for mode 2 (f)
+// in: doubles for mode 0 / 1 (difference array, histogram), floats for mode 2 (f);
+// f_hi, f_lo (optional): f as BF16 hi and lo planes of row length ld
 cudaError_t launch_fwd_epilogue(const void *in, int in_stride, const float *W, int nW, int n_lo, const TimeDev &tm,
-                                int mode, int K, float *s, float *f_out, cudaStream_t st);
+                                int mode, int K, float *s, float *f_out, cudaStream_t st, uint16_t *f_hi = nullptr,
+                                uint16_t *f_lo = nullptr, int ld = 0);
 cudaError_t launch_adj_conv(const float *in, int from_v, const float *W, int nW, int n_lo, const TimeDev &tm, int mode,
                             int K, void *out, cudaStream_t st);
 // wpb: warps (4x4x2 voxel bricks) per CTA, 2, 4 or 8

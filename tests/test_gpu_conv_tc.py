@@ -111,3 +111,50 @@ def test_recon_with_tensor_core_plan(api, oracle_mod):
     x30 = plan.recon(s, x0, iters=30, lambda_R=0.0)
     r30 = float((plan.forward(x30) - s).norm())
     assert float(x30.min()) >= 0.0 and r30 < 0.5 * r0
+
+
+# ---------------------------------------------------------------------------
+# Split-plane forward (the kernel pat_forward uses on tensor-core plans): f as
+# BF16 hi and lo planes, 128 x 256 tiles brought in by tensor-map copies,
+# persistent CTAs with two TMEM accumulators.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("L,n_angles,n_el", [(1024, 2, 3), (300, 10, 8), (129, 3, 43), (1024, 8, 40),
+                                             (2048, 20, 128)])
+def test_conv_forward_split_planes(api, oracle_mod, L, n_angles, n_el):
+    """L = 1024, 300 (ragged last tile, a row length that is not a multiple
+    of 8 fine bins: 3300), 129; K = 6, 80, 129 (inside one 256-row tile),
+    320 (two tiles, the second ragged) and 2560 with L 2048 (10 x 16 = 160
+    tiles: more than one per CTA, both accumulators and both ring slots
+    cycling)."""
+    w = W.small_cylinder(n_vox=4, n_angles=n_angles, n_el=n_el, L=L)
+    taps = oracle_mod.taps_for(w)
+    plan = api.Plan(w, taps=taps, conv_tc=True, allow_clip=True)
+    rng = np.random.default_rng(L + n_el)
+    f = rng.standard_normal((w.K, w.UL)).astype(np.float32)
+    ft = torch.from_numpy(f).cuda()
+    planes = plan.conv_split(ft)
+    s = plan.conv_forward_split(planes).cpu().numpy()
+    s_ref = oracle_mod.conv_forward(w, taps, f.astype(np.float64))
+    e = rel(s, s_ref)
+    print(f"K {w.K} L {L}: split-plane forward rel L2 {e:.3e}")
+    assert e <= TC_TOL, e
+    # the same split products as the FP32-input kernel: agreement to FP32 accumulation order
+    s_fp32in = plan.conv_forward(ft).cpu().numpy()
+    assert rel(s, s_fp32in) <= 1e-5, rel(s, s_fp32in)
+    assert api._lib.pat_plan_get_info(plan.handle)["tc_error"] == 0
+
+
+def test_split_planes_layout(api, oracle_mod):
+    """hi = bf16(f), lo = bf16(f - hi), rows of ld = U L rounded up to 8, zero padding."""
+    w = W.small_cylinder(n_vox=4, n_angles=3, n_el=4, L=300)
+    plan = api.Plan(w, taps=oracle_mod.taps_for(w), conv_tc=True, allow_clip=True)
+    f = torch.randn(w.K, w.UL, device="cuda", generator=torch.Generator(device="cuda").manual_seed(3))
+    planes = plan.conv_split(f)
+    ld = -(-w.UL // 8) * 8
+    assert planes.numel() * 2 >= 2 * w.K * ld * 2
+    p = planes[:2 * w.K * ld].view(2, w.K, ld)
+    hi = p[0].view(torch.bfloat16).float()
+    lo = p[1].view(torch.bfloat16).float()
+    assert torch.equal(hi[:, :w.UL], f.to(torch.bfloat16).float())
+    assert torch.equal(lo[:, :w.UL], (f - hi[:, :w.UL]).to(torch.bfloat16).float())
+    assert float(p[:, :, w.UL:].abs().max()) == 0.0

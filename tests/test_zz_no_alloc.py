@@ -46,8 +46,8 @@ def _call_static(_lib, plan, x, s):
                                           (lambda: W.small_cylinder(n_vox=12, n_angles=4, n_el=3), True)],
                          ids=["plane", "cylinder", "cylinder-tensor-core-conv"])
 def test_static_forward_matches_forward(parts, make, conv_tc):
-    """With conv_tc the scratch also holds f (K U L floats after the FP64
-    difference array), which the tensor-core convolution reads."""
+    """With conv_tc the scratch also holds f as BF16 hi and lo planes after
+    the FP64 difference array, which the tensor-core convolution reads."""
     _lib, api, orc = parts
     w = make()
     plan = api.Plan(w, taps=orc.taps_for(w), conv_tc=conv_tc)
@@ -74,8 +74,9 @@ def test_static_forward_rejects_oversize_plan(parts):
 
 def test_static_forward_rejects_tensor_core_f_beyond_limit(parts):
     """704 c1 positions: the difference array alone, K (U L + 1) 8 bytes,
-    fits the fixed array; with the tensor-core convolution's f, K U L 4 bytes
-    more, it does not, and only that plan is rejected."""
+    fits the fixed array; with the tensor-core convolution's f planes, K ld 4
+    bytes more (ld = U L rounded up to a multiple of 8), it does not, and only
+    that plan is rejected."""
     _lib, api, orc = parts
     w = W.c1()
     w = w.with_tx(np.tile(w.tx, (22, 1)))
@@ -89,4 +90,4 @@ def test_static_forward_rejects_tensor_core_f_beyond_limit(parts):
     assert _call_static(_lib, plain, x, s) == 0, _lib.load().pat_last_error()
     torch.cuda.synchronize()
     assert _call_static(_lib, tc, x, s) == _lib.PAT_ERR_WORKSPACE
-    assert b"K U L 4 bytes" in _lib.load().pat_last_error()
+    assert b"K ld 4 bytes" in _lib.load().pat_last_error()
