@@ -40,13 +40,14 @@ N_ANGLES = 180
 # FP32 floating-point operations of one quadrant-edge area evaluation of the
 # cylinder path: 2 per FFMA, 1 per FADD / FMUL, 4 per FFMA2, 2 per FADD2 /
 # FMUL2 (MUFU operations not counted), from the instruction counters of one
-# adj_geom_kernel launch on the c2 geometry (64^3 grid, 128 positions,
-# 1.450e9 evaluations): 165.5 (166.4 for the forward kernel).
-FLOPS_PER_QUAD_EVAL = 166
+# adj_geom_kernel launch of this kernel version on the c2 geometry (64^3
+# grid, 128 positions, 1.450e9 evaluations): 162.0 (161.6 for the forward
+# kernel).
+FLOPS_PER_QUAD_EVAL = 162
 # DRAM read + write bytes of one adj_geom_kernel launch of the default
 # workload (128^3 x 512 positions), one-pass ncu capture of this kernel
-# version (29.38 MB read + 16.85 MB written).
-ADJ_TRAFFIC_BYTES = 41.94e6  # adj_geom_kernel DRAM read + write per launch (ncu, full c2 batch)
+# version (31.43 MB read + 16.23 MB written).
+ADJ_TRAFFIC_BYTES = 47.66e6  # adj_geom_kernel DRAM read + write per launch (ncu, full c2 batch)
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
