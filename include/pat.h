@@ -233,6 +233,17 @@ pat_status pat_conv_adjoint(pat_plan *plan, const float *s, float *v, void *stre
  * pat_plan_info.tc_error. */
 pat_status pat_conv_split(pat_plan *plan, const float *f, uint16_t *planes, void *stream);
 pat_status pat_conv_forward_split(pat_plan *plan, const uint16_t *planes, float *s, void *stream);
+/* Test of the tensor-core kernels' give-up path, with no fault and no endless
+ * wait: pat_conv_forward_split's kernel on one CTA, its epilogue withholding
+ * the release of the first TMEM accumulator, so that the bounded wait for it
+ * (about two seconds) runs out at the third output tile.  The kernel then
+ * stops every warp, waits (bounded) for the copies and MMAs it issued,
+ * frees its TMEM and leaves; pat_plan_info.tc_error becomes non-zero and s
+ * is undefined.  Needs a plan with at least 3 output tiles
+ * (ceil(L / 128) ceil(K / 256) >= 3; else PAT_ERR_INVALID_ARG).
+ * pat_plan_clear_tc_error resets tc_error to 0 (asynchronous on stream). */
+pat_status pat_conv_forward_split_withheld(pat_plan *plan, const uint16_t *planes, float *s, void *stream);
+pat_status pat_plan_clear_tc_error(pat_plan *plan, void *stream);
 /* z[N] = transpose of the geometric assembly applied to v[K][U L] (Alg. 7 / Alg. 6). */
 pat_status pat_adjoint_geometric(pat_plan *plan, const float *v, float *z, void *ws, size_t ws_bytes, void *stream);
 

@@ -59,7 +59,8 @@ class pat_plan_info(C.Structure):
 
 EXPORTS = ["pat_system_kernel", "pat_system_kernel_dc", "pat_plan_create", "pat_plan_destroy", "pat_plan_get_info",
            "pat_workspace_bytes", "pat_forward", "pat_adjoint", "pat_forward_geometric", "pat_conv_forward",
-           "pat_conv_adjoint", "pat_conv_split", "pat_conv_forward_split", "pat_adjoint_geometric", "pat_forward_dc", "pat_recon", "pat_recon_batch",
+           "pat_conv_adjoint", "pat_conv_split", "pat_conv_forward_split", "pat_conv_forward_split_withheld",
+           "pat_plan_clear_tc_error", "pat_adjoint_geometric", "pat_forward_dc", "pat_recon", "pat_recon_batch",
            "pat_plan_autotune", "pat_forward_static", "pat_measure_peaks", "pat_last_error", "pat_version"]
 
 _lock = threading.Lock()
@@ -100,9 +101,12 @@ def load(build_if_missing: bool = True):
         for nm in ("pat_forward", "pat_adjoint", "pat_forward_geometric", "pat_adjoint_geometric"):
             getattr(L, nm).restype = st
             getattr(L, nm).argtypes = [vp, vp, vp, vp, C.c_size_t, vp]
-        for nm in ("pat_conv_forward", "pat_conv_adjoint", "pat_conv_split", "pat_conv_forward_split"):
+        for nm in ("pat_conv_forward", "pat_conv_adjoint", "pat_conv_split", "pat_conv_forward_split",
+                   "pat_conv_forward_split_withheld"):
             getattr(L, nm).restype = st
             getattr(L, nm).argtypes = [vp, vp, vp, vp]
+        L.pat_plan_clear_tc_error.restype = st
+        L.pat_plan_clear_tc_error.argtypes = [vp, vp]
         L.pat_forward_static.restype = st
         L.pat_forward_static.argtypes = [vp, vp, vp, vp]
         L.pat_recon.restype = st
@@ -216,6 +220,14 @@ def pat_conv_split(plan, f, planes, stream=None):
 
 def pat_conv_forward_split(plan, planes, s, stream=None):
     check(load().pat_conv_forward_split(plan, _ptr(planes), _ptr(s), _stream(stream)))
+
+
+def pat_conv_forward_split_withheld(plan, planes, s, stream=None):
+    check(load().pat_conv_forward_split_withheld(plan, _ptr(planes), _ptr(s), _stream(stream)))
+
+
+def pat_plan_clear_tc_error(plan, stream=None):
+    check(load().pat_plan_clear_tc_error(plan, _stream(stream)))
 
 
 def pat_recon(plan, s, x, iters, lambda_R, step, ws, stream=None):

@@ -119,6 +119,16 @@ class Plan:
         _lib.pat_conv_forward_split(self.handle, planes, s)
         return s
 
+    def conv_forward_split_withheld(self, planes: torch.Tensor) -> torch.Tensor:
+        """The give-up path of the split-plane kernel (pat_conv_forward_split_withheld):
+        s is undefined afterwards and info["tc_error"] non-zero."""
+        s = torch.empty((self.K, self.L), dtype=torch.float32, device=self.device)
+        _lib.pat_conv_forward_split_withheld(self.handle, planes, s)
+        return s
+
+    def clear_tc_error(self) -> None:
+        _lib.pat_plan_clear_tc_error(self.handle)
+
     def conv_adjoint(self, s: torch.Tensor) -> torch.Tensor:
         s = self._f32(s, self.K * self.L)
         v = torch.empty((self.K, self.UL), dtype=torch.float32, device=self.device)

@@ -625,6 +625,30 @@ extern "C" pat_status pat_conv_forward_split(pat_plan *p, const uint16_t *planes
     return PAT_OK;
 }
 
+extern "C" pat_status pat_conv_forward_split_withheld(pat_plan *p, const uint16_t *planes, float *s, void *stream)
+{
+    g_err.clear();
+    if (!p || !planes || !s) return fail(PAT_ERR_INVALID_ARG, "pat_conv_forward_split_withheld: null pointer");
+    if (!p->tc) return fail(PAT_ERR_UNSUPPORTED, "pat_conv_forward_split_withheld: the plan has no tensor-core convolution");
+    if (((uintptr_t)planes & 15) != 0)
+        return fail(PAT_ERR_INVALID_ARG, "pat_conv_forward_split_withheld: planes must be 16-byte aligned");
+    const int ntiles = ((p->tm.L + kTcM - 1) / kTcM) * ((p->K + kTcN2 - 1) / kTcN2);
+    if (ntiles < 3)
+        return fail(PAT_ERR_INVALID_ARG, "pat_conv_forward_split_withheld: needs at least 3 output tiles, the plan has %d",
+                    ntiles);
+    CK(launch_conv_tc_fwd2(planes, planes + (size_t)p->tcg.ld * p->K, p->tc_fwd2_tab, p->tcg, p->K, p->tm.L, p->tm.U, s,
+                           p->tc_err, (cudaStream_t)stream, true));
+    return PAT_OK;
+}
+
+extern "C" pat_status pat_plan_clear_tc_error(pat_plan *p, void *stream)
+{
+    g_err.clear();
+    if (!p) return fail(PAT_ERR_INVALID_ARG, "pat_plan_clear_tc_error: null pointer");
+    if (p->tc) CK(cudaMemsetAsync(p->tc_err, 0, sizeof(int), (cudaStream_t)stream));
+    return PAT_OK;
+}
+
 extern "C" pat_status pat_conv_adjoint(pat_plan *p, const float *s, float *v, void *stream)
 {
     g_err.clear();

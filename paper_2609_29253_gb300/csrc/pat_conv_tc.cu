@@ -683,7 +683,9 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_adj_kernel(const float *__
 // `tempty`, so that the MMAs of the next tile overlap the store.  Every wait
 // is bounded (about 2 s, or as soon as another thread has given up); a
 // thread that gives up records an error, waits (bounded) for what it issued
-// and leaves.
+// and leaves.  withhold != 0 (a test of that path, one CTA): the epilogue
+// does not release the first accumulator, so the MMA warp's wait for it at
+// the third tile runs out.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -760,7 +762,7 @@ __device__ __forceinline__ void fwd2_abort(const Fwd2 &R, int *err, int code)
 __global__ void __launch_bounds__(kTcThreadsFwd2, 1)
     conv_tc_fwd2_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
                         const uint8_t *__restrict__ Tf, int nst, int m0a, int K, int L, int U,
-                        float *__restrict__ s, int *__restrict__ err)
+                        float *__restrict__ s, int *__restrict__ err, int withhold)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     if (smem_u32(smem_raw) & 1023u) { // swizzled operand tiles need 1024-byte alignment
@@ -896,7 +898,7 @@ __global__ void __launch_bounds__(kTcThreadsFwd2, 1)
             }
             fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(R.tempty[a]);
+            if (lane == 0 && !(withhold && ti == 0)) mbar_arrive(R.tempty[a]);
         }
     }
     fence_before();
@@ -1071,7 +1073,7 @@ cudaError_t launch_split_bf16(const float *f, int K, int UL, int ld, uint16_t *h
 }
 
 cudaError_t launch_conv_tc_fwd2(const uint16_t *hi, const uint16_t *lo, const uint8_t *Tf2, const TcGeometry &g, int K,
-                                int L, int U, float *s, int *err, cudaStream_t st)
+                                int L, int U, float *s, int *err, cudaStream_t st, bool withhold)
 {
     CUtensorMap mh, ml;
     cudaError_t e = plane_map(&mh, hi, K, U * L, g.ld);
@@ -1081,8 +1083,10 @@ cudaError_t launch_conv_tc_fwd2(const uint16_t *hi, const uint16_t *lo, const ui
                              (int)g.fwd2_smem);
     if (e != cudaSuccess) return e;
     const int ntiles = ((L + kM - 1) / kM) * ((K + kN2 - 1) / kN2);
-    const unsigned grid = (unsigned)std::max(1, std::min(ntiles, g.sms));
-    conv_tc_fwd2_kernel<<<grid, kTcThreadsFwd2, g.fwd2_smem, st>>>(mh, ml, Tf2, g.nst_fwd2, g.m0a, K, L, U, s, err);
+    if (withhold && ntiles < 3) return cudaErrorInvalidValue; // the withheld release is waited for at the third tile
+    const unsigned grid = withhold ? 1u : (unsigned)std::max(1, std::min(ntiles, g.sms));
+    conv_tc_fwd2_kernel<<<grid, kTcThreadsFwd2, g.fwd2_smem, st>>>(mh, ml, Tf2, g.nst_fwd2, g.m0a, K, L, U, s, err,
+                                                                     withhold ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -48,7 +48,9 @@ cudaError_t launch_conv_tc_adj(const float *s, const uint8_t *Ta, const TcGeomet
 cudaError_t launch_split_bf16(const float *f, int K, int UL, int ld, uint16_t *hi, uint16_t *lo, cudaStream_t st);
 // s [K][L] from the hi and lo planes (16-byte aligned, rows of g.ld, only the
 // first U L columns of a row read): the persistent tensor-map / tcgen05 kernel.
+// withhold: a test of its give-up path on one CTA (at least 3 tiles; s is
+// then undefined and *err becomes non-zero after about two seconds).
 cudaError_t launch_conv_tc_fwd2(const uint16_t *hi, const uint16_t *lo, const uint8_t *Tf2, const TcGeometry &g, int K,
-                                int L, int U, float *s, int *err, cudaStream_t st);
+                                int L, int U, float *s, int *err, cudaStream_t st, bool withhold = false);
 
 } // namespace pat

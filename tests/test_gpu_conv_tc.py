@@ -158,3 +158,39 @@ def test_split_planes_layout(api, oracle_mod):
     assert torch.equal(hi[:, :w.UL], f.to(torch.bfloat16).float())
     assert torch.equal(lo[:, :w.UL], (f - hi[:, :w.UL]).to(torch.bfloat16).float())
     assert float(p[:, :, w.UL:].abs().max()) == 0.0
+
+
+def test_split_plane_give_up_path(api, oracle_mod):
+    """The bounded waits of the tensor-core kernels, made to run out without a
+    fault or an endless wait: with the release of the first accumulator
+    withheld, the MMA warp gives up at the third tile after about two seconds;
+    the kernel stops, frees its TMEM and reports through tc_error.  The plan
+    stays usable: after clearing the error, the next call matches the FP64
+    convolution with tc_error 0."""
+    w = W.small_cylinder(n_vox=4, n_angles=2, n_el=3, L=1024)  # 8 output tiles, one CTA
+    taps = oracle_mod.taps_for(w)
+    plan = api.Plan(w, taps=taps, conv_tc=True, allow_clip=True)
+    rng = np.random.default_rng(5)
+    f = rng.standard_normal((w.K, w.UL)).astype(np.float32)
+    planes = plan.conv_split(torch.from_numpy(f).cuda())
+    assert api._lib.pat_plan_get_info(plan.handle)["tc_error"] == 0
+    plan.conv_forward_split_withheld(planes)
+    torch.cuda.synchronize()
+    assert api._lib.pat_plan_get_info(plan.handle)["tc_error"] != 0
+    plan.clear_tc_error()
+    torch.cuda.synchronize()
+    assert api._lib.pat_plan_get_info(plan.handle)["tc_error"] == 0
+    s = plan.conv_forward_split(planes).cpu().numpy()
+    s_ref = oracle_mod.conv_forward(w, taps, f.astype(np.float64))
+    assert rel(s, s_ref) <= TC_TOL, rel(s, s_ref)
+    assert api._lib.pat_plan_get_info(plan.handle)["tc_error"] == 0
+
+
+def test_give_up_test_needs_three_tiles(api, oracle_mod):
+    """pat_conv_forward_split_withheld refuses a plan whose single CTA would not
+    reach the withheld accumulator (fewer than 3 output tiles)."""
+    w = W.small_cylinder(n_vox=4, n_angles=2, n_el=3, L=256)  # 2 output tiles
+    plan = api.Plan(w, taps=oracle_mod.taps_for(w), conv_tc=True, allow_clip=True)
+    planes = plan.conv_split(torch.zeros(w.K, w.UL, device="cuda"))
+    with pytest.raises(Exception, match="3 output tiles"):
+        plan.conv_forward_split_withheld(planes)
