@@ -234,6 +234,7 @@ struct BinWindow {
 struct FwdSurfaceSink {
     BinWindow w;
     float x, prev;
+    __device__ __forceinline__ void start(int) {}
     __device__ __forceinline__ void pre(int, int) {}
     __device__ __forceinline__ void group(int e0, int, float val, float)
     {
@@ -252,6 +253,7 @@ struct FwdSurfaceSink {
 struct FwdDerivSink {
     BinWindow w, wd;
     float x, prev, dprev;
+    __device__ __forceinline__ void start(int) {}
     __device__ __forceinline__ void pre(int, int) {}
     __device__ __forceinline__ void group(int e0, int, float val, float dval)
     {
@@ -663,18 +665,11 @@ struct AdjSurfaceSink {
     const float2 *__restrict__ P;
     int UL;
     float acc;
-    float2 pe;  // P at the current group start
+    float2 pe;  // P at the current group start, loaded by start()
     float2 pn;  // P at its end, loaded by pre()
-    bool have;
     __device__ __forceinline__ int clampi(int e) const { return min(max(e, 0), UL); }
-    __device__ __forceinline__ void pre(int e0, int e1)
-    {
-        if (!have) {
-            pe = __ldg(&P[clampi(e0)]);
-            have = true;
-        }
-        pn = __ldg(&P[clampi(e1)]);
-    }
+    __device__ __forceinline__ void start(int e) { pe = __ldg(&P[clampi(e)]); }
+    __device__ __forceinline__ void pre(int, int e1) { pn = __ldg(&P[clampi(e1)]); }
     __device__ __forceinline__ void group(int, int, float val, float)
     {
         acc = fmaf(val, (pn.x - pe.x) + (pn.y - pe.y), acc);
@@ -717,7 +712,7 @@ __global__ void __launch_bounds__(kThreads, geom_min_ctas(KIND, false)) adj_geom
                 acc += (double)s.acc;
             } else {
                 AdjSurfaceSink s{(const float2 *)Pv + (size_t)rows[k] * stride, tm.UL, 0.f, make_float2(0.f, 0.f),
-                                 make_float2(0.f, 0.f), false};
+                                 make_float2(0.f, 0.f)};
                 surface_pair<KIND, false, area_mode(METHOD)>(t, tm, ix, iy, iz, s, glx, glw);
                 acc += (double)s.acc;
             }
