@@ -279,8 +279,9 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
     size_t need_epi = sizeof(float) * (size_t)(tm.UL + p->nW) + 64;
     size_t need_adj = sizeof(float) * (size_t)(tm.L + p->nW + tm.UL) + 64;
     if (need_epi > (size_t)optin || need_adj > (size_t)optin) {
+        const int ul = tm.UL; // tm lives in *p
         delete p;
-        return fail(PAT_ERR_UNSUPPORTED, "U L = %d needs %zu bytes of shared memory per block, device has %d", tm.UL,
+        return fail(PAT_ERR_UNSUPPORTED, "U L = %d needs %zu bytes of shared memory per block, device has %d", ul,
                     need_adj, optin);
     }
 
