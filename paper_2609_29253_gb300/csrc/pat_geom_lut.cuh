@@ -138,12 +138,15 @@ __device__ __forceinline__ float2 lut_end_diff(const LutDev &L, const LutEdge &e
     return ff_sub(Eb, Ea);
 }
 
+// The record of one quadrant, kept small: the group loop indexes the
+// records of a pair dynamically, so they live in the thread's stack frame,
+// whose lines are evicted to DRAM as CTAs turn over; the squares of s and v
+// are formed where they are used instead of stored (the same float-float
+// products, so the same values).
 struct LutQuad {
     float2 umin, umax; // angular bounds (FP32 fold; pi itself in float-float)
-    float2 smin, smax; // sin(umin/2), sin(umax/2)
-    float2 Smin, Smax; // their squares, the clamp thresholds of S = sin^2(u/2)
+    float2 smin, smax; // sin(umin/2), sin(umax/2); their squares are the clamp thresholds of S = sin^2(u/2)
     float2 vmin, vmax; // axial bounds (v itself, not shifted)
-    float2 vmin2, vmax2;
 };
 
 // Clamped inverse Phi-hat(v, r) of Eq. (alphabeta), with s = sin(u/2) at it.
@@ -153,11 +156,11 @@ struct LutQuad {
 __device__ __forceinline__ float2 lut_bound(const LutQuad &Q, float2 q, float2 v2, float2 inv4, float2 &s)
 {
     const float2 S = ff_mul(ff_sub(q, v2), inv4);
-    if (!ff_lt(Q.Smin, S)) {
+    if (!ff_lt(ff_sqr(Q.smin), S)) {
         s = Q.smin;
         return Q.umin;
     }
-    if (!ff_lt(S, Q.Smax)) {
+    if (!ff_lt(S, ff_sqr(Q.smax))) {
         s = Q.smax;
         return Q.umax;
     }
@@ -204,10 +207,6 @@ __device__ __forceinline__ void cyl_pair_lut(const TxDev &t, const TimeDev &tm, 
             act[2 * a + b] = a < nu && ff_lt(c.umin, c.umax) && ff_lt(c.vmin, c.vmax); // else zero area
             c.smin = sin_half_ff(c.umin);
             c.smax = sin_half_ff(c.umax);
-            c.Smin = ff_sqr(c.smin);
-            c.Smax = ff_sqr(c.smax);
-            c.vmin2 = ff_sqr(c.vmin);
-            c.vmax2 = ff_sqr(c.vmax);
             Fp[2 * a + b] = ff_mul(c.umin, ff_sub(c.vmax, c.vmin)); // Phi-hat = umin before the sweep
         }
     // q = r^2 - (R - rho)^2 = q_b + tt (2 r_b + tt), tt = r - r_b
@@ -235,8 +234,8 @@ __device__ __forceinline__ void cyl_pair_lut(const TxDev &t, const TimeDev &tm, 
                 F = ff_add(ff_mul(c.umax, ff_sub(b, c.vmin)), ff_mul(c.umin, ff_sub(c.vmax, b)));
             } else {
                 float2 sa, sb;
-                const float2 al = lut_bound(c, q, c.vmax2, inv4, sa); // alpha = Phi-hat(v_max)
-                const float2 be = lut_bound(c, q, c.vmin2, inv4, sb); // beta = Phi-hat(v_min)
+                const float2 al = lut_bound(c, q, ff_sqr(c.vmax), inv4, sa); // alpha = Phi-hat(v_max)
+                const float2 be = lut_bound(c, q, ff_sqr(c.vmin), inv4, sb); // beta = Phi-hat(v_min)
                 F = ff_sub(ff_mul(al, c.vmax), ff_mul(be, c.vmin));
                 if (ff_lt(al, be)) F = ff_add(F, ff_mul(ed.pref, lut_end_diff(L, ed, sb, sa)));
             }
