@@ -48,6 +48,9 @@ FLOPS_PER_QUAD_EVAL = 157
 # workload (128^3 x 512 positions), one-pass ncu capture of this kernel
 # version (32.23 MB read + 23.72 MB written).
 ADJ_TRAFFIC_BYTES = 55.95e6  # adj_geom_kernel DRAM read + write per launch (ncu, full c2 batch)
+# FP32 flops executed per planar quadrant-edge evaluation by adj_geom_kernel on
+# the c3 line's 128 positions (same counters): 89.5 (88.1 for the forward).
+FLOPS_PER_PLANE_EVAL = 89.5
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -439,6 +442,17 @@ def fista_compare(api, dev, first, n_prob, iters, power):
             "timing": "wall clock per iteration over all problems, host to device completion, step sizes fixed"}
 
 
+def plane_roofline(quad_evals, ms):
+    """FP32 roofline of a planar A^T (its geometry kernel is 99 % of it): the
+    executed flops per evaluation measured with ncu's counters, over the FP32
+    peak at the maximum SM clock."""
+    ach = quad_evals * FLOPS_PER_PLANE_EVAL / (ms * 1e-3) / 1e12
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2070.0 * 1e6 / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "flops_per_unit": FLOPS_PER_PLANE_EVAL, "units": quad_evals,
+            "unit_name": "planar quadrant-edge area evaluation", "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+
+
 def c3_line(api, dev, n_pos):
     """The precision-split system (c3): 256^3 voxels at 0.08 mm, planar 3x3 mm
     elements on a 40 mm hemisphere, L 2048, tcgen05 BF16 split convolution;
@@ -466,6 +480,7 @@ def c3_line(api, dev, n_pos):
             "plain_fp32": {"ms": {"forward": t_pf, "adjoint": t_pa},
                            "forward_pairs_per_s": pairs / (t_pf * 1e-3), "adjoint_pairs_per_s": pairs / (t_pa * 1e-3)},
             "rel_l2_split_vs_plain_fp32": {"forward": rel_l2(s, s_p), "adjoint": rel_l2(z, z_p)},
+            "roofline_adjoint_geometry": plane_roofline(plan.info["quad_evals"], t_a),
             "tc_error": api._lib.pat_plan_get_info(plan.handle)["tc_error"]}
 
 
