@@ -28,13 +28,20 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA library cannot be built")
 
 
+# -ftz=true: FP32 subnormals flush to zero.  No FP32 quantity of the operator
+# comes near the subnormal range (squared distances of micrometres and more,
+# angles of the aperture), and without the flag every reciprocal square root
+# carries a subnormal rescaling (compare, select, multiply) that the
+# issue-bound geometry kernels pay for: 1-4 % slower, bit-identical results.
 def _flags(extra=()):
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
+    return ARCH + ["-O3", "-ftz=true", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
                    "-I", CSRC] + list(extra)
 
 
 def _deps():
-    return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "pat.h")]
+    # the sources, the header, and this file (its flags)
+    return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "pat.h"),
+                                                                 os.path.abspath(__file__)]
 
 
 def _stale(target, deps):
