@@ -330,7 +330,8 @@ struct FwdPointSink {
 // distances, so the window stays small however far the element's bins spread
 // over the grid.  False when no pair has a bin in [0, U L].  With x, also the
 // largest |x| over the run's voxels into s_lohi[2] (as bits: |x| >= 0 orders
-// as its bit pattern), read in the same pass.
+// as its bit pattern; infinite if any value is not finite), read in the same
+// pass.
 template <int KIND>
 __device__ bool fwd_window(const TxDev &t, const TimeDev &tm, const GridDev &g, const SuperTile &stl, long long b0,
                            long long b1, int span, int &base, int &top, int *s_lohi, const float *x = nullptr)
@@ -347,7 +348,10 @@ __device__ bool fwd_window(const TxDev &t, const TimeDev &tm, const GridDev &g, 
     for (long long br = b0 + warp; br < b1; br += kWarpsPerBlock) { // warp-uniform trip count
         int ix, iy, iz;
         if (tile_voxel(g, stl, br, lane, ix, iy, iz)) {
-            if (x) xm = fmaxf(xm, fabsf(x[((long long)iz * g.ny + iy) * g.nx + ix]));
+            if (x) { // a non-finite value (NaN included) makes the maximum infinite
+                const float a = fabsf(x[((long long)iz * g.ny + iy) * g.nx + ix]);
+                xm = a <= 3.40282347e38f ? fmaxf(xm, a) : __int_as_float(0x7f800000);
+            }
             int b_lo, b_hi;
             pair_bins_fast<KIND>(t, tm, ix, iy, iz, b_lo, b_hi);
             lo = min(lo, b_lo);
@@ -407,11 +411,13 @@ __global__ void __launch_bounds__(kThreads, geom_min_ctas(KIND, true)) fwd_geom_
     // swept area of the aperture), so that no partial sum of the at most 2^14
     // differences a bin receives from the CTA's pairs comes near 2^62
     float scale = 1.f;
+    bool bad = false; // a non-finite x: the window's rows get NaN, as FP64 arithmetic would give
     if (kFixed) {
         const float bound = __uint_as_float((unsigned)s_lohi[2]) * (12.8f * t.R * t.Lz);
+        bad = !(bound <= 3.40282347e38f);
         int q = 0;
-        frexpf(bound, &q);
-        scale = bound > 0.f ? ldexpf(1.f, 46 - q) : 1.f;
+        frexpf(bad ? 1.f : bound, &q);
+        scale = bound > 0.f && !bad ? ldexpf(1.f, 46 - q) : 1.f;
     }
     __syncthreads();
     for (long long br = b0 + warp; br < b1; br += kWarpsPerBlock) { // warp-uniform trip count
@@ -436,7 +442,7 @@ __global__ void __launch_bounds__(kThreads, geom_min_ctas(KIND, true)) fwd_geom_
     double *row = Dg + (size_t)rows[k] * n + win.base;
     const double *wd = (const double *)sD;
     const long long *wl = (const long long *)sD;
-    const double iscale = 1.0 / (double)scale; // a power of two: exact
+    const double iscale = bad ? __longlong_as_double(0x7ff8000000000000LL) : 1.0 / (double)scale; // 2^-k: exact
     if (gridDim.x == 1 && exclusive) {
         for (int i = threadIdx.x; i < m; i += blockDim.x) row[i] = kFixed ? (double)wl[i] * iscale : wd[i];
     } else {

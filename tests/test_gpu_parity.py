@@ -330,3 +330,17 @@ def test_recon_decreases_objective(api, orc):
     x40 = plan.recon(s, x0, iters=40, lambda_R=lam)
     assert float(x40.min()) >= 0.0
     assert obj(x40) < obj(x5) < obj(x0)
+
+
+@pytest.mark.parametrize("value", [float("nan"), float("inf")])
+def test_non_finite_voxel_propagates(api, orc, value):
+    """A NaN or infinite voxel value reaches the output as in FP64 arithmetic,
+    on the cylinder forward (whose window is in fixed point) and on planes;
+    the other outputs of a plan with finite x stay finite."""
+    for w in (W.small_cylinder(n_vox=8, n_angles=2, n_el=3), W.c1().with_(n=(8, 8, 8), origin=W.centred_origin((8, 8, 8), 0.1e-3))):
+        plan = api.Plan(w, taps=orc.taps_for(w))
+        x = torch.rand(w.N, device="cuda", generator=torch.Generator(device="cuda").manual_seed(2))
+        assert bool(torch.isfinite(plan.forward(x)).all())
+        x[w.N // 2] = value
+        s = plan.forward(x)
+        assert not bool(torch.isfinite(s).all())
