@@ -252,8 +252,9 @@ struct FwdSurfaceSink {
 // scaled by the CTA's power of two, is rounded once to an int64, and the
 // group adds the exact integer difference to the one before with an int64
 // shared atomic (native, where the FP64 shared addition above is a
-// compare-and-swap loop on the FP64 pipe).  The telescoping sums stay exact;
-// the quantum is 2^-46 of a bound of the CTA's shares.  Measured: the c2
+// compare-and-swap loop on the FP64 pipe).  x arrives normalized by the CTA's
+// power of two.  The telescoping sums stay exact; the quantum is 2^-46 of a
+// bound of the CTA's shares.  Measured: the c2
 // forward 4.5 % faster, c5's first positions and Exp-1's trapezoidal rule 2 %
 // slower; on planes, whose group loop is short, the conversion costs more than
 // the loop it removes (c3 5 % slower), so planar kernels keep the FP64 window.
@@ -405,19 +406,29 @@ __global__ void __launch_bounds__(kThreads, geom_min_ctas(KIND, true)) fwd_geom_
     const int m = win.top - win.base + 1;
     for (int b = threadIdx.x; b < 2 * m; b += blockDim.x) sD[b] = 0.f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // cylinder surface kernels: the fixed-point window (FwdFixedSink) with the
-    // scale 2^(46 - q), 2^q above max |x| over the CTA's voxels (from the
-    // window pass) times a bound of the element's area (about 12 times the
-    // swept area of the aperture), so that no partial sum of the at most 2^14
-    // differences a bin receives from the CTA's pairs comes near 2^62
-    float scale = 1.f;
+    // cylinder surface kernels: the fixed-point window (FwdFixedSink).  x is
+    // normalized by 2^-qx (max |x| over the CTA's voxels, from the window pass,
+    // below 2^qx; with subnormals flushed 2^-qx is an FP32 number) and the
+    // shares by 2^(46 - qa), 2^qa above a bound of the element's area (12.8 R
+    // Lz, about 12 times the swept area of the aperture), so that every scaled
+    // share stays below 2^46 and no partial sum of the at most 2^14 differences
+    // a bin receives from the CTA's pairs comes near 2^62; the flush undoes
+    // both in FP64.
+    float xscale = 1.f, scale = 1.f;
+    double iscale = 1.0;
     bool bad = false; // a non-finite x: the window's rows get NaN, as FP64 arithmetic would give
     if (kFixed) {
-        const float bound = __uint_as_float((unsigned)s_lohi[2]) * (12.8f * t.R * t.Lz);
-        bad = !(bound <= 3.40282347e38f);
-        int q = 0;
-        frexpf(bad ? 1.f : bound, &q);
-        scale = bound > 0.f && !bad ? ldexpf(1.f, 46 - q) : 1.f;
+        const float xmax = __uint_as_float((unsigned)s_lohi[2]);
+        bad = !(xmax <= 3.40282347e38f);
+        int qx = 0, qa = 0;
+        if (!bad && xmax > 0.f) frexpf(xmax, &qx);
+        frexpf(12.8f * t.R * t.Lz, &qa);
+        // both powers of two stay normal FP32 numbers: |x| near FLT_MAX moves
+        // the rest of its exponent into the share scale, which only shrinks
+        const int ex = -min(qx, 125), es = min(46 - qa - (qx + ex), 126);
+        xscale = ldexpf(1.f, ex);
+        scale = ldexpf(1.f, es);
+        iscale = bad ? __longlong_as_double(0x7ff8000000000000LL) : ldexp(1.0, -ex - es); // exact
     }
     __syncthreads();
     for (long long br = b0 + warp; br < b1; br += kWarpsPerBlock) { // warp-uniform trip count
@@ -429,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, geom_min_ctas(KIND, true)) fwd_geom_
                 point_pair<KIND>(t, tm, ix, iy, iz, s);
                 s.flush();
             } else if (kFixed) {
-                FwdFixedSink s{win, xv, scale, 0};
+                FwdFixedSink s{win, xv * xscale, scale, 0};
                 surface_pair<KIND, false, area_mode(METHOD)>(t, tm, ix, iy, iz, s, glx, glw);
             } else {
                 FwdSurfaceSink s{win, xv, 0.f};
@@ -442,7 +453,6 @@ __global__ void __launch_bounds__(kThreads, geom_min_ctas(KIND, true)) fwd_geom_
     double *row = Dg + (size_t)rows[k] * n + win.base;
     const double *wd = (const double *)sD;
     const long long *wl = (const long long *)sD;
-    const double iscale = bad ? __longlong_as_double(0x7ff8000000000000LL) : 1.0 / (double)scale; // 2^-k: exact
     if (gridDim.x == 1 && exclusive) {
         for (int i = threadIdx.x; i < m; i += blockDim.x) row[i] = kFixed ? (double)wl[i] * iscale : wd[i];
     } else {

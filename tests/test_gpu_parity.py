@@ -344,3 +344,22 @@ def test_non_finite_voxel_propagates(api, orc, value):
         x[w.N // 2] = value
         s = plan.forward(x)
         assert not bool(torch.isfinite(s).all())
+
+
+@pytest.mark.parametrize("k", [1e-22, 1e-12, 1e12, 1e22])
+def test_forward_linearity_extreme_scales(api, orc, k):
+    """A_geo (k x) = k A_geo x at extreme scales of x, on the cylinder forward
+    (its window in fixed point with per-CTA scales from max |x|; for this
+    element, 12.8 R Lz = 3.8e-5, a single FP32 power of two would overflow
+    below max |x| = 1e-20) and on planes.  Compared on the fine-bin rows f
+    (areas of order 1e-10..1e-8 per unit x), whose scaled values stay normal
+    FP32 numbers; the convolved outputs are about 1e-16 per unit x and would
+    underflow FP32 at the smallest k on any path."""
+    for w in (W.small_cylinder(n_vox=8, n_angles=2, n_el=3), W.c1().with_(n=(8, 8, 8), origin=W.centred_origin((8, 8, 8), 0.1e-3))):
+        plan = api.Plan(w, taps=orc.taps_for(w))
+        x = torch.rand(w.N, device="cuda", generator=torch.Generator(device="cuda").manual_seed(4))
+        f1 = plan.forward_geometric(x).double()
+        fk = plan.forward_geometric(x * k).double() / k
+        assert float(f1.norm()) > 0.0
+        rel = float((fk - f1).norm() / f1.norm())
+        assert rel <= 1e-6, (w.name, rel)
