@@ -260,13 +260,13 @@ struct FwdSurfaceSink {
 // the loop it removes (c3 5 % slower), so planar kernels keep the FP64 window.
 struct FwdFixedSink {
     BinWindow w;
-    float x, scale;
+    float xs; // x times both powers of two (exact)
     long long prev;
     __device__ __forceinline__ void start(int) {}
     __device__ __forceinline__ void pre(int, int) {}
     __device__ __forceinline__ void group(int e0, int, float val, float)
     {
-        const long long v = __float2ll_rn(x * val * scale);
+        const long long v = __float2ll_rn(xs * val);
         if (v != prev) atomicAdd((unsigned long long *)w.hi + w.idx(e0), (unsigned long long)(v - prev));
         prev = v;
     }
@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, geom_min_ctas(KIND, true)) fwd_geom_
                 point_pair<KIND>(t, tm, ix, iy, iz, s);
                 s.flush();
             } else if (kFixed) {
-                FwdFixedSink s{win, xv * xscale, scale, 0};
+                FwdFixedSink s{win, xv * xscale * scale, 0};
                 surface_pair<KIND, false, area_mode(METHOD)>(t, tm, ix, iy, iz, s, glx, glw);
             } else {
                 FwdSurfaceSink s{win, xv, 0.f};
@@ -740,7 +740,8 @@ struct AdjSurfaceSink {
     __device__ __forceinline__ void pre(int, int e1) { pn = __ldg(&P[clampi(e1)]); }
     __device__ __forceinline__ void group(int, int, float val, float)
     {
-        acc = fmaf(val, (pn.x - pe.x) + (pn.y - pe.y), acc);
+        const float2 d = __ffma2_rn(pe, make_float2(-1.f, -1.f), pn); // pn - pe, both parts in one instruction
+        acc = fmaf(val, d.x + d.y, acc);
         pe = pn;
     }
     __device__ __forceinline__ void finish(int) {}
