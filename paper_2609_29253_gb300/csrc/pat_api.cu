@@ -269,6 +269,11 @@ extern "C" pat_status pat_plan_create(pat_plan **out, const pat_grid *grid, cons
     p->tc = (params->flags & PAT_FLAG_CONV_TC) != 0;
     if (p->tc) {
         p->tcg = tc_geometry(n_taps, params->U, params->L, n_lo);
+        // power-of-two scale of the operand tables: the largest tap times
+        // 2^tscale in [1, 2) (every combined tap W is a mean of U taps)
+        double tmax = 0.0;
+        for (int i = 0; i < n_taps; ++i) tmax = std::max(tmax, std::fabs(taps_host[i]));
+        if (tmax > 0.0 && std::isfinite(tmax)) p->tcg.tscale = std::min(100, std::max(-100, -std::ilogb(tmax)));
         const size_t need_tc = std::max(std::max(p->tcg.fwd_smem, p->tcg.adj_smem), p->tcg.fwd2_smem);
         if (need_tc > (size_t)optin) {
             delete p;
@@ -561,13 +566,17 @@ static pat_status enqueue_forward(pat_plan *p, const float *x, float *s, float *
 static pat_status enqueue_adjoint(pat_plan *p, const float *in, int from_v, float *z, void *ws, cudaStream_t st)
 {
     int mode = p->tm.method == PAT_METHOD_POINT ? 1 : 0;
+    double vscale = 1.0;
     if (p->tc && !from_v) {
+        // v stays scaled by the tables' 2^tscale (of the signal's size, far
+        // from FP32's smallest normal) and is unscaled in FP64 as it is read
         float *vw = (float *)((char *)ws + ws_P(p));
-        CK(launch_conv_tc_adj(in, p->tc_adj_tab, p->tcg, p->K, p->tm.L, p->tm.U, vw, p->tc_err, st));
+        CK(launch_conv_tc_adj(in, p->tc_adj_tab, p->tcg, p->K, p->tm.L, p->tm.U, vw, p->tc_err, st, false));
         in = vw;
         from_v = 1;
+        vscale = ldexp(1.0, -p->tcg.tscale);
     }
-    CK(launch_adj_conv(in, from_v, p->W, p->nW, p->n_lo, p->tm, mode, p->K, ws, st));
+    CK(launch_adj_conv(in, from_v, p->W, p->nW, p->n_lo, p->tm, mode, p->K, ws, st, vscale));
     CK(launch_adj_geom(p->tx, p->Kf, p->rows, p->kind_all, p->tm, p->g, ws, z, st, p->adj_wpb));
     return PAT_OK;
 }

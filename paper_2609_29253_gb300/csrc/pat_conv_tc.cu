@@ -446,7 +446,7 @@ __device__ __forceinline__ void ring_abort(const Ring &R, int *err, int code)
 
 __global__ void __launch_bounds__(kTcThreadsFwd, 1)
     conv_tc_fwd_kernel(const float *__restrict__ f, const uint8_t *__restrict__ Tf, int nst, int m0off, int K, int L,
-                       int UL, int U, float *__restrict__ s, int *__restrict__ err)
+                       int UL, int U, float *__restrict__ s, int *__restrict__ err, float oscale)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     if (smem_u32(smem_raw) & 1023u) { // swizzled operand tiles need 1024-byte alignment
@@ -564,8 +564,8 @@ __global__ void __launch_bounds__(kTcThreadsFwd, 1)
                     for (int j = 0; j < 16; ++j) {
                         const int k = k0 + c + j;
                         if (k < K) {
-                            if (split) atomicAdd(&s[(long long)k * L + l], r[j]);
-                            else s[(long long)k * L + l] = r[j];
+                            if (split) atomicAdd(&s[(long long)k * L + l], r[j] * oscale);
+                            else s[(long long)k * L + l] = r[j] * oscale;
                         }
                     }
                 }
@@ -586,7 +586,8 @@ __global__ void __launch_bounds__(kTcThreadsFwd, 1)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kTcThreads) conv_tc_adj_kernel(const float *__restrict__ s, const uint8_t *__restrict__ Ta,
                                                                  int nst, int d0, int K, int L, int UL, int U,
-                                                                 float *__restrict__ v, int *__restrict__ err)
+                                                                 float *__restrict__ v, int *__restrict__ err,
+                                                                 float oscale)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     if (smem_u32(smem_raw) & 1023u) { // swizzled operand tiles need 1024-byte alignment
@@ -639,7 +640,7 @@ __global__ void __launch_bounds__(kTcThreads) conv_tc_adj_kernel(const float *__
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int k = k0 + c + j;
-                    if (k < K) v[(long long)k * UL + (long long)U * m + p] = r[j];
+                    if (k < K) v[(long long)k * UL + (long long)U * m + p] = r[j] * oscale;
                 }
             }
         }
@@ -762,7 +763,7 @@ __device__ __forceinline__ void fwd2_abort(const Fwd2 &R, int *err, int code)
 __global__ void __launch_bounds__(kTcThreadsFwd2, 1)
     conv_tc_fwd2_kernel(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
                         const uint8_t *__restrict__ Tf, int nst, int m0a, int K, int L, int U,
-                        float *__restrict__ s, int *__restrict__ err, int withhold)
+                        float *__restrict__ s, int *__restrict__ err, int withhold, float oscale)
 {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     if (smem_u32(smem_raw) & 1023u) { // swizzled operand tiles need 1024-byte alignment
@@ -892,7 +893,7 @@ __global__ void __launch_bounds__(kTcThreadsFwd2, 1)
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int k = k0 + c + j;
-                        if (k < K) s[(long long)k * L + l] = r[j];
+                        if (k < K) s[(long long)k * L + l] = r[j] * oscale;
                     }
                 }
             }
@@ -950,7 +951,7 @@ __device__ __forceinline__ void put_split(uint8_t *stage, int row, int kk, doubl
 
 // Tf[st]: element (i, kk) = W[U i + nW - 1 - (st kKS + kk - shift)] (zero for
 // the shift's leading columns: a window that starts shift bins early)
-__global__ void tc_table_fwd_kernel(const double *__restrict__ taps, int T, int U, int nst, int shift,
+__global__ void tc_table_fwd_kernel(const double *__restrict__ taps, int T, int U, int nst, int shift, double sc,
                                     uint8_t *__restrict__ Tf)
 {
     const long long n = (long long)nst * kM * kKS;
@@ -958,12 +959,12 @@ __global__ void tc_table_fwd_kernel(const double *__restrict__ taps, int T, int 
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         const int st = (int)(e / (kM * kKS)), r = (int)(e % (kM * kKS)), i = r / kKS, kk = r % kKS;
         const int mu = st * kKS + kk - shift;
-        put_split(Tf + (size_t)st * 2 * kAHalf, i, kk, w64(taps, T, U, U * i + nW - 1 - mu));
+        put_split(Tf + (size_t)st * 2 * kAHalf, i, kk, w64(taps, T, U, U * i + nW - 1 - mu) * sc);
     }
 }
 
 // Ta[p][st]: element (i, kk) = W[U (d0 + lambda - i) + c - p], lambda = st kKS + kk
-__global__ void tc_table_adj_kernel(const double *__restrict__ taps, int T, int U, int nst, int d0, int c,
+__global__ void tc_table_adj_kernel(const double *__restrict__ taps, int T, int U, int nst, int d0, int c, double sc,
                                     uint8_t *__restrict__ Ta)
 {
     const long long n = (long long)U * nst * kM * kKS;
@@ -972,7 +973,7 @@ __global__ void tc_table_adj_kernel(const double *__restrict__ taps, int T, int 
         const int r = (int)(e % (kM * kKS)), i = r / kKS, kk = r % kKS;
         const int p = (int)(g / nst), st = (int)(g % nst);
         const int lam = st * kKS + kk;
-        put_split(Ta + (size_t)g * 2 * kAHalf, i, kk, w64(taps, T, U, U * (d0 + lam - i) + c - p));
+        put_split(Ta + (size_t)g * 2 * kAHalf, i, kk, w64(taps, T, U, U * (d0 + lam - i) + c - p) * sc);
     }
 }
 
@@ -1015,15 +1016,17 @@ TcGeometry tc_geometry(int T, int U, int L, int n_lo)
     g.fwd2_table_bytes = (size_t)g.nst_fwd2 * 2 * kAHalf;
     g.fwd2_smem = (size_t)kRing2 * kSlot2 + 8 * (2 * kRing2 + 6) + 1024;
     g.ld = (U * L + 7) / 8 * 8;
+    g.tscale = 0;
     return g;
 }
 
 cudaError_t launch_tc_tables(const double *taps, int T, int U, const TcGeometry &g, uint8_t *Tf, uint8_t *Ta,
                              uint8_t *Tf2, cudaStream_t st)
 {
-    tc_table_fwd_kernel<<<304, 256, 0, st>>>(taps, T, U, g.nst_fwd, 0, Tf);
-    tc_table_adj_kernel<<<608, 256, 0, st>>>(taps, T, U, g.nst_adj, g.d0, g.c, Ta);
-    tc_table_fwd_kernel<<<304, 256, 0, st>>>(taps, T, U, g.nst_fwd2, g.shift, Tf2);
+    const double sc = ldexp(1.0, g.tscale); // exact
+    tc_table_fwd_kernel<<<304, 256, 0, st>>>(taps, T, U, g.nst_fwd, 0, sc, Tf);
+    tc_table_adj_kernel<<<608, 256, 0, st>>>(taps, T, U, g.nst_adj, g.d0, g.c, sc, Ta);
+    tc_table_fwd_kernel<<<304, 256, 0, st>>>(taps, T, U, g.nst_fwd2, g.shift, sc, Tf2);
     return cudaGetLastError();
 }
 
@@ -1086,7 +1089,7 @@ cudaError_t launch_conv_tc_fwd2(const uint16_t *hi, const uint16_t *lo, const ui
     if (withhold && ntiles < 3) return cudaErrorInvalidValue; // the withheld release is waited for at the third tile
     const unsigned grid = withhold ? 1u : (unsigned)std::max(1, std::min(ntiles, g.sms));
     conv_tc_fwd2_kernel<<<grid, kTcThreadsFwd2, g.fwd2_smem, st>>>(mh, ml, Tf2, g.nst_fwd2, g.m0a, K, L, U, s, err,
-                                                                     withhold ? 1 : 0);
+                                                                     withhold ? 1 : 0, ldexpf(1.f, -g.tscale));
     return cudaGetLastError();
 }
 
@@ -1104,18 +1107,20 @@ cudaError_t launch_conv_tc_fwd(const float *f, const uint8_t *Tf, const TcGeomet
         if (e != cudaSuccess) return e;
     }
     dim3 grid(gx, gy, (unsigned)nsplit);
-    conv_tc_fwd_kernel<<<grid, kTcThreadsFwd, g.fwd_smem, st>>>(f, Tf, g.nst_fwd, g.m0off, K, L, U * L, U, s, err);
+    conv_tc_fwd_kernel<<<grid, kTcThreadsFwd, g.fwd_smem, st>>>(f, Tf, g.nst_fwd, g.m0off, K, L, U * L, U, s, err,
+                                                                ldexpf(1.f, -g.tscale));
     return cudaGetLastError();
 }
 
 cudaError_t launch_conv_tc_adj(const float *s, const uint8_t *Ta, const TcGeometry &g, int K, int L, int U, float *v,
-                               int *err, cudaStream_t st)
+                               int *err, cudaStream_t st, bool unscale)
 {
     cudaError_t e = cudaFuncSetAttribute((const void *)conv_tc_adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)g.adj_smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((L + kM - 1) / kM), (unsigned)((K + kN - 1) / kN));
-    conv_tc_adj_kernel<<<grid, kTcThreads, g.adj_smem, st>>>(s, Ta, g.nst_adj, g.d0, K, L, U * L, U, v, err);
+    conv_tc_adj_kernel<<<grid, kTcThreads, g.adj_smem, st>>>(s, Ta, g.nst_adj, g.d0, K, L, U * L, U, v, err,
+                                                             unscale ? ldexpf(1.f, -g.tscale) : 1.f);
     return cudaGetLastError();
 }
 

@@ -670,11 +670,14 @@ __global__ void __launch_bounds__(kThreads) fwd_dc_epilogue_kernel(const double 
 
 // ---------------------------------------------------------------------------
 // adjoint: v = h-bar^- * upsample^T(s); mode 0: P[b] = sum_{b'<b} wgt v (float2
-// hi/lo), mode 1: w = U Fs v (point method), mode 2: v itself.
+// hi/lo), mode 1: w = U Fs v (point method), mode 2: v itself.  from_v: v
+// given, times vscale (in FP64; a power of two undoes the tensor-core
+// adjoint's table scale exactly).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) adj_conv_kernel(const float *__restrict__ s, int from_v,
                                                             const float *__restrict__ Wg, int nW, int n_lo,
-                                                            TimeDev tm, int mode, void *__restrict__ out)
+                                                            TimeDev tm, int mode, void *__restrict__ out,
+                                                            double vscale)
 {
     extern __shared__ float sm[];
     __shared__ double tmp[kWarpsPerBlock];
@@ -698,7 +701,8 @@ __global__ void __launch_bounds__(kThreads) adj_conv_kernel(const float *__restr
         long long hi = b - c0 + nW - 1;
         int l1 = (int)min((long long)L - 1, hi >= 0 ? hi / U : -1LL);
         double acc = 0.0;
-        if (from_v) acc = (double)s[(size_t)k * UL + b]; // v given (stage entry point)
+        if (from_v) acc = (double)s[(size_t)k * UL + b] * vscale; // v given (stage entry point, or the
+                                                                   // tensor-core adjoint's scaled v)
         else
             for (int l = l0; l <= l1; ++l) acc = fma((double)ss[l], (double)W[U * l + c0 - b], acc);
         if (mode == 0) {
@@ -740,8 +744,7 @@ struct AdjSurfaceSink {
     __device__ __forceinline__ void pre(int, int e1) { pn = __ldg(&P[clampi(e1)]); }
     __device__ __forceinline__ void group(int, int, float val, float)
     {
-        const float2 d = __ffma2_rn(pe, make_float2(-1.f, -1.f), pn); // pn - pe, both parts in one instruction
-        acc = fmaf(val, d.x + d.y, acc);
+        acc = fmaf(val, (pn.x - pe.x) + (pn.y - pe.y), acc);
         pe = pn;
     }
     __device__ __forceinline__ void finish(int) {}
@@ -1151,11 +1154,11 @@ cudaError_t launch_fwd_epilogue(const void *in, int in_stride, const float *W, i
 }
 
 cudaError_t launch_adj_conv(const float *s, int from_v, const float *W, int nW, int n_lo, const TimeDev &tm, int mode,
-                            int K, void *out, cudaStream_t st)
+                            int K, void *out, cudaStream_t st, double vscale)
 {
     size_t smem = sizeof(float) * (size_t)(tm.L + nW + (mode == 0 ? tm.UL : 0));
     set_smem_attr((const void *)adj_conv_kernel, smem);
-    adj_conv_kernel<<<K, kThreads, smem, st>>>(s, from_v, W, nW, n_lo, tm, mode, out);
+    adj_conv_kernel<<<K, kThreads, smem, st>>>(s, from_v, W, nW, n_lo, tm, mode, out, vscale);
     return cudaGetLastError();
 }
 

@@ -35,8 +35,9 @@ cudaError_t launch_fwd_geom(const TxDev *tx, int Kf, int K, const int *rows, int
 cudaError_t launch_fwd_epilogue(const void *in, int in_stride, const float *W, int nW, int n_lo, const TimeDev &tm,
                                 int mode, int K, float *s, float *f_out, cudaStream_t st, uint16_t *f_hi = nullptr,
                                 uint16_t *f_lo = nullptr, int ld = 0);
+// from_v: in is v [K][U L], multiplied by vscale in FP64 as it is read
 cudaError_t launch_adj_conv(const float *in, int from_v, const float *W, int nW, int n_lo, const TimeDev &tm, int mode,
-                            int K, void *out, cudaStream_t st);
+                            int K, void *out, cudaStream_t st, double vscale = 1.0);
 // wpb: warps (4x4x2 voxel bricks) per CTA, 2, 4 or 8
 cudaError_t launch_adj_geom(const TxDev *tx, int K, const int *rows, int kind, const TimeDev &tm, const GridDev &g,
                             const void *P, float *z, cudaStream_t st, int wpb = kWarpsPerBlock);

@@ -89,6 +89,29 @@ def test_operator_tensor_cores(api, oracle_mod, mk):
     assert plan.info["tc_error"] == 0 and api._lib.pat_plan_get_info(plan.handle)["tc_error"] == 0
 
 
+def test_adjoint_tensor_cores_physical_scale(api, oracle_mod):
+    """A^T of the operator's own output, s = A x of order 1e-16 for x of order
+    1 (the system kernel in SI units is of order 1e-20): v = h-bar^- * s is then
+    near 1e-36, and the products of the BF16 split, about 2^-8 of v, would fall
+    below FP32's smallest normal (1.2e-38) in the tensor cores; the operand
+    tables carry a power-of-two scale that keeps them of the signal's size.
+    Checked on the stage (v) and on the whole A^T (z)."""
+    w = W.small_cylinder(n_vox=10, n_angles=4, n_el=3)
+    taps = oracle_mod.taps_for(w)
+    plan = api.Plan(w, taps=taps, conv_tc=True)
+    s_ref, _ = oracle_mod.forward(w, taps, w.x.astype(np.float64))
+    s32 = s_ref.astype(np.float32)
+    assert 1e-18 < float(np.abs(s32).max()) < 1e-13
+    v = plan.conv_adjoint(torch.from_numpy(s32).cuda()).cpu().numpy()
+    v_ref = oracle_mod.conv_adjoint(w, taps, s32.astype(np.float64))
+    assert float(np.abs(v_ref).max()) < 1e-33  # the regime in question
+    assert rel(v, v_ref) <= TC_TOL, rel(v, v_ref)
+    z = plan.adjoint(torch.from_numpy(s32).cuda()).cpu().numpy()
+    z_ref, _ = oracle_mod.adjoint(w, taps, s32.astype(np.float64))
+    assert rel(z, z_ref) <= TC_TOL, rel(z, z_ref)
+    assert api._lib.pat_plan_get_info(plan.handle)["tc_error"] == 0
+
+
 def test_dot_product_tensor_cores(api, oracle_mod):
     w = W.small_cylinder(n_vox=8, n_angles=4, n_el=3)
     plan = api.Plan(w, taps=oracle_mod.taps_for(w), conv_tc=True)
