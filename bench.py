@@ -41,12 +41,13 @@ N_ANGLES = 180
 # cylinder path: 2 per FFMA, 1 per FADD / FMUL, 4 per FFMA2, 2 per FADD2 /
 # FMUL2 (MUFU operations not counted), from the instruction counters of one
 # adj_geom_kernel launch of this kernel version on the c2 geometry (64^3
-# grid, 128 positions, 1.450e9 evaluations).
+# grid, 128 positions, 1.450e9 evaluations): 143.0 (134.9 for the forward
+# kernel with its fixed-point window).
 FLOPS_PER_QUAD_EVAL = 143.0
 # DRAM read + write bytes of one adj_geom_kernel launch of the default
 # workload (128^3 x 512 positions), one-pass ncu capture of this kernel
-# version.
-ADJ_TRAFFIC_BYTES = 80.25e6  # adj_geom_kernel DRAM read + write per launch (ncu, full c2 batch)
+# version (32.61 MB read + 44.06 MB written).
+ADJ_TRAFFIC_BYTES = 76.67e6  # adj_geom_kernel DRAM read + write per launch (ncu, full c2 batch)
 # FP32 flops executed per planar quadrant-edge evaluation by adj_geom_kernel on
 # the c3 line's 128 positions (same counters): 87.1 (86.0 for the forward).
 FLOPS_PER_PLANE_EVAL = 87.1

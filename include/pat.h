@@ -71,7 +71,11 @@ enum { PAT_EIR_GAUSS_SINE = 0, PAT_EIR_BOX = 1 };
  *                        (hi + lo), hi*hi + hi*lo + lo*hi accumulated in FP32.
  *                        Areas and accumulation of f stay FP32 / FP64; the
  *                        convolution then carries about 16 significant bits
- *                        per product instead of FP64 accumulation;
+ *                        per product instead of FP64 accumulation.  The
+ *                        operand tables hold the taps times a power of two
+ *                        (the largest in [1, 2)), undone exactly on the
+ *                        outputs, so that no product nears FP32's smallest
+ *                        normal for taps of SI size (about 1e-20);
  *   PAT_FLAG_PIECEWISE_PLANES  the paper's Piecewise-Planes approximation
  *                        (Sec. 4.3): every cylindrical element is replaced by
  *                        np_planes planes tangent at the centres of equal
