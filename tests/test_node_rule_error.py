@@ -116,3 +116,70 @@ def test_two_nodes_would_not_hold_at_5L():
     worst, count = _worst(2, 5.0, 6.0)
     assert count > 0
     assert worst > 3 * 1.1e-7, worst
+
+
+def _subst(near, a, b, ts, tf, f):
+    """6 Gauss-Legendre nodes in tau after t = t_s - c tau^2 (near: the S = 0
+    branch point at or beyond b) or t = t_f + c tau^2 (the X = 0 one at or
+    before a), tau over [t0, 1] so that the map covers exactly [a, b]."""
+    x, w = _rule(6)
+    if near:
+        c = ts - a
+        t0 = math.sqrt((ts - b) / c)
+    else:
+        c = b - tf
+        t0 = math.sqrt((a - tf) / c)
+    tau = t0 + (1.0 - t0) * x
+    t = ts - c * tau**2 if near else tf + c * tau**2
+    return float(np.sum(w * 2.0 * c * tau * (1.0 - t0) * f(t)))
+
+
+def test_substitution_rule_within_L():
+    """Branch points closer than L: the substitution at the near one, or with
+    both within L the piece halved at its midpoint, each half taking its own
+    end's substitution.  The truncation error of the rule itself (FP64
+    emulation) stays below 1e-10 of the piece integral, branch point on the
+    piece's end included; the kernels' FP32 rounding comes on top of it."""
+    worst, count = 0.0, 0
+    for rho in RHO:
+        four = 4.0 * R * rho
+        for vc in VC:
+            for L in LEN:
+                a, b = 0.0, L
+                for side in ("s", "f"):
+                    for k in np.linspace(0.0, 0.99, 12):
+                        if side == "s":
+                            t = b + k * L
+                            qp = t * (2.0 * vc + t)  # S = 0 at t
+                        else:
+                            t = a - k * L
+                            if t + vc < 0.0:
+                                continue  # v_f >= 0 on a folded quadrant
+                            qp = four + t * (2.0 * vc + t)  # X = 0 at t
+                        S0, S1 = qp / four, (qp - L * (2.0 * vc + L)) / four
+                        if not (-1e-15 <= S1 < S0 <= 1.0 + 1e-15) or (S1 < 0.5 < S0):
+                            continue
+                        ts = max(math.sqrt(qp + vc * vc) - vc, b)
+                        qf = four - qp
+                        hasf = qf < vc * vc
+                        tf = min(math.sqrt(max(0.0, vc * vc - qf)) - vc, a) if hasf else -vc
+                        near, far = ts - b < L, hasf and a - tf < L
+                        if not (near or far):
+                            continue
+                        low = S0 <= 0.5
+
+                        def f(tt, four=four, qp=qp, vc=vc, low=low):
+                            S = (qp - tt * (2.0 * vc + tt)) / four
+                            u = 2.0 * np.arcsin(np.sqrt(np.clip(S, 0.0, 1.0)))
+                            return u if low else math.pi - u
+
+                        if near and far:
+                            m = 0.5 * (a + b)
+                            got = _subst(False, a, m, ts, tf, f) + _subst(True, m, b, ts, tf, f)
+                        else:
+                            got = _subst(near, a, b, ts, tf, f)
+                        ref, _ = integrate.quad(lambda tt: float(f(tt)), a, b, epsabs=0.0, epsrel=1e-13, limit=500)
+                        worst = max(worst, abs(got - ref) / abs(ref))
+                        count += 1
+    assert count > 300, count
+    assert worst <= 1e-10, worst
