@@ -44,6 +44,12 @@ N_ANGLES = 180
 # grid, 128 positions, 1.450e9 evaluations): 143.0 (134.9 for the forward
 # kernel with its fixed-point window).
 FLOPS_PER_QUAD_EVAL = 143.0
+# Warp instructions issued per evaluation by the same launch (smsp__inst_executed:
+# 1.0578e10 for 1.450e9 evaluations): the kernel is bound by instruction issue,
+# so the line also reports the fraction of the SMs' issue slots it fills
+# (152 SMs x 4 schedulers x 1 warp instruction per cycle).
+WARP_INSTS_PER_QUAD_EVAL = 7.2947
+ISSUE_PER_SM_PER_CYCLE = 4
 # DRAM read + write bytes of one adj_geom_kernel launch of the default
 # workload (128^3 x 512 positions), one-pass ncu capture of this kernel
 # version (32.61 MB read + 44.06 MB written).
@@ -361,6 +367,18 @@ def conv_all_rows(api, taps, dev):
                                    "tiles": (-(-w.L // 128)) * (-(-w.K // 256))},
            "tc_error": api._lib.pat_plan_get_info(tc.handle)["tc_error"]}
     return out
+
+
+def issue_line(quad_evals, seconds, sm_mhz):
+    """Issue-slot view of the dominant kernel beside its FP32 roofline: warp
+    instructions issued per launch (the per-evaluation count from the
+    instruction counters times the plan's evaluations) over the launch's
+    CUDA-event time, against 152 SMs x 4 schedulers x one instruction per cycle
+    at the clock seen."""
+    got = quad_evals * WARP_INSTS_PER_QUAD_EVAL / seconds / 1e9
+    peak = SM_COUNT * ISSUE_PER_SM_PER_CYCLE * sm_mhz * 1e6 / 1e9
+    return {"achieved": got, "peak": peak, "unit": "G warp instructions/s", "frac": got / peak,
+            "warp_insts_per_unit": WARP_INSTS_PER_QUAD_EVAL}
 
 
 def measured_hbm_gbs():
@@ -795,7 +813,8 @@ def main():
                              "kernel": "adj_geom_kernel", "flops_per_unit": FLOPS_PER_QUAD_EVAL,
                              "units_per_launch": qe, "unit_name": "quadrant-edge area evaluation",
                              "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load",
-                             "measured_peaks": measured},
+                             "measured_peaks": measured,
+                             "issue": issue_line(qe, mean_adj, sm_mhz)},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 4 * args.steps,
                 "clocks": clk, "wall_s_timed": t_wall}
         line.update(extras)
