@@ -252,8 +252,9 @@ struct FwdSurfaceSink {
 // scaled by the CTA's power of two, is rounded once to an int64, and the
 // group adds the exact integer difference to the one before with an int64
 // shared atomic (native, where the FP64 shared addition above is a
-// compare-and-swap loop on the FP64 pipe).  x arrives normalized by the CTA's
-// power of two.  The telescoping sums stay exact; the quantum is 2^-46 of a
+// compare-and-swap loop on the FP64 pipe).  x arrives multiplied by the CTA's
+// two powers of two (its normalization and the share scale), so a share costs
+// one multiply.  The telescoping sums stay exact; the quantum is 2^-46 of a
 // bound of the CTA's shares.  Measured: the c2
 // forward 4.5 % faster, c5's first positions and Exp-1's trapezoidal rule 2 %
 // slower; on planes, whose group loop is short, the conversion costs more than
