@@ -40,15 +40,15 @@ N_ANGLES = 180
 # FP32 floating-point operations of one quadrant-edge area evaluation of the
 # cylinder path: 2 per FFMA, 1 per FADD / FMUL, 4 per FFMA2, 2 per FADD2 /
 # FMUL2 (MUFU operations not counted), from the instruction counters of one
-# adj_geom_kernel launch of this kernel version on the c2 geometry (64^3
-# grid, 128 positions, 1.450e9 evaluations): 143.0 (134.9 for the forward
-# kernel with its fixed-point window).
-FLOPS_PER_QUAD_EVAL = 143.0
+# adj_geom_kernel launch of this kernel version on the c2 geometry at the
+# bench's grid (128^3 voxels, one angle of 128 positions, 1.1629e10
+# evaluations): 139.5 (143.0 on a 64^3 grid).
+FLOPS_PER_QUAD_EVAL = 139.5
 # Warp instructions issued per evaluation by the same launch (smsp__inst_executed:
-# 1.0578e10 for 1.450e9 evaluations): the kernel is bound by instruction issue,
+# 7.639e10 for 1.1629e10 evaluations): the kernel is bound by instruction issue,
 # so the line also reports the fraction of the SMs' issue slots it fills
 # (152 SMs x 4 schedulers x 1 warp instruction per cycle).
-WARP_INSTS_PER_QUAD_EVAL = 7.2947
+WARP_INSTS_PER_QUAD_EVAL = 6.569
 ISSUE_PER_SM_PER_CYCLE = 4
 # DRAM read + write bytes of one adj_geom_kernel launch of the default
 # workload (128^3 x 512 positions), one-pass ncu capture of this kernel
